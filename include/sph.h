@@ -1,0 +1,176 @@
+/*
+ * sph.h -- C ABI of libsph, the GB300 (sm_103a) SPH neighbour-interaction
+ * hot path after Schaller, Gonnet, Chalk, Draper, "SWIFT: Using task-based
+ * parallelism, fully asynchronous communication, and graph partition-based
+ * domain decomposition for strong scaling on more than 100,000 cores",
+ * PASC '16.
+ *
+ * Problem statement (Section 2): particles with position x, velocity v,
+ * internal energy u, mass m and smoothing length h in a periodic box. The
+ * density stage solves each h_i so that the weighted neighbour number
+ * N_i(h) = (4 pi / 3) h^3 sum_j W(r_ij, h) equals n_ngb, and evaluates
+ * rho_i (Eq. rho), Omega_i and P_i; the force stage evaluates Eqs. (dvdt) and
+ * (dudt); the integrator task (Section 3.1) updates positions and velocities.
+ * W is the cubic spline with support radius h (W(r,h) = (8/pi) w(r/h) / h^3,
+ * w(q) = 1 - 6q^2 + 6q^3 below q = 1/2, 2(1-q)^3 up to q = 1).
+ *
+ * Conventions shared by every call:
+ *   - Return value: 0 (SPH_OK) on success, else a negative SPH_E* code;
+ *     sph_last_error() then holds a one-line message.
+ *   - Device pointers are CUDA global-memory addresses on the device that was
+ *     current when sph_create() ran; host pointers are ordinary host memory.
+ *   - All work is enqueued on the stream given to sph_create(). Calls that
+ *     must decide on device results (the smoothing-length iteration, status
+ *     reads, sph_stats) synchronise that stream; the others return as soon as
+ *     the work is enqueued.
+ *   - Ownership: the caller owns every buffer it passes and keeps it alive
+ *     for the duration of the call; the library copies inputs into its own
+ *     particle store (sorted by cell) and never frees caller memory. Results
+ *     come back in the caller's original particle order.
+ *   - Particle arrays are in "caller order": particle k of box b is entry
+ *     box_offsets[b] + k. Vectors are row-major [N][3].
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPH_OK 0
+#define SPH_EINVAL (-1)        /* bad argument (null pointer, N < 1, h <= 0, m <= 0, u < 0, box <= 0) */
+#define SPH_ENOMEM (-2)        /* device allocation failed or workspace too small */
+#define SPH_ECUDA (-3)         /* a CUDA runtime call failed */
+#define SPH_ENOTCONVERGED (-4) /* smoothing-length iteration hit max_iter */
+#define SPH_EBOXTOOSMALL (-5)  /* some h would exceed L/3 of its box */
+#define SPH_ENONPHYSICAL (-6)  /* rho <= 0, Omega <= 0 or u <= 0 */
+#define SPH_ETIMEOUT (-7)      /* a bounded device-side wait gave up */
+#define SPH_ESTATE (-8)        /* call out of order (e.g. sph_force before sph_density) */
+
+/* ---- fields for sph_get ---- */
+#define SPH_X 0      /* double [N][3] positions (wrapped into [0, L)) */
+#define SPH_V 1      /* float  [N][3] velocities */
+#define SPH_U 2      /* float  [N]    internal energy per unit mass */
+#define SPH_H 3      /* double [N]    smoothing lengths */
+#define SPH_RHO 4    /* float  [N]    density, Eq. (rho) */
+#define SPH_OMEGA 5  /* float  [N]    Omega = 1 + h/(3 rho) drho/dh */
+#define SPH_P 6      /* float  [N]    pressure P = (gamma - 1) rho u */
+#define SPH_A 7      /* float  [N][3] dv/dt, Eq. (dvdt) */
+#define SPH_DUDT 8   /* float  [N]    du/dt, Eq. (dudt) */
+#define SPH_NNGB 9   /* int32  [N]    #{j != i : r_ij < h_i} at the converged h */
+#define SPH_NITER 10 /* int32  [N]    density passes the particle's h needed */
+#define SPH_NFORCE 11 /* int32 [N]    #{j != i : r_ij < max(h_i, h_j)} */
+#define SPH_M 12     /* float  [N]    masses */
+#define SPH_NFIELDS 13
+
+/* ---- interaction-kernel forms ---- */
+#define SPH_MODE_PLAIN 0   /* one launch per density pass, host-driven h iteration */
+#define SPH_MODE_BATCHED 1 /* persistent work-queue kernels, in-kernel h iteration, CUDA graph */
+
+/* ---- precision ---- */
+#define SPH_PREC_FP32 0  /* FP32 pair arithmetic and accumulation */
+#define SPH_PREC_KAHAN 1 /* FP32 pair arithmetic, compensated (Kahan) accumulation */
+
+typedef struct sph_ctx sph_ctx; /* opaque, owned by the library */
+
+typedef struct {
+  double gamma;    /* adiabatic index (P = (gamma - 1) rho u) */
+  double n_ngb;    /* target weighted neighbour number (> 32/3) */
+  double h_tol;    /* converged when |N_i - n_ngb| <= h_tol * n_ngb */
+  int max_iter;    /* density passes before SPH_ENOTCONVERGED */
+  int n_split;     /* split octree cells holding more particles than this (8..256) */
+  int precision;   /* SPH_PREC_* */
+  int mode;        /* SPH_MODE_* */
+  int reserved[4]; /* zero */
+} sph_params;
+
+typedef struct {
+  int64_t n_particles;
+  int64_t n_boxes;
+  int64_t n_top_cells;        /* cells of the top grids (edge >= largest h) */
+  int64_t n_leaves;           /* octree leaves after recursive splitting */
+  int64_t n_pairs_density;    /* leaf-pair tasks in the density lists */
+  int64_t n_pairs_force;      /* leaf-pair tasks in the force lists */
+  int64_t density_interactions; /* sum_i #{j != i: r_ij < h_i}, converged pass */
+  int64_t force_interactions;   /* sum_i #{j != i: r_ij < max(h_i, h_j)} */
+  int64_t density_pair_candidates; /* (i, j) pairs tested in all density passes */
+  int64_t force_pair_candidates;   /* (i, j) pairs tested in the force pass */
+  int32_t density_passes;     /* density passes of the last sph_density */
+  int32_t rebuilds;           /* grid / list rebuilds in the last sph_density */
+  int32_t max_iter_used;      /* most passes any particle needed */
+  int32_t reserved;
+  double h_min, h_max;        /* extremes of the converged h */
+} sph_stats_t;
+
+/* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,
+ * n_split = 64, FP32, batched mode. */
+void sph_default_params(sph_params *p);
+
+/* Create a context on the current CUDA device. `cuda_stream` is a
+ * cudaStream_t (NULL: the legacy default stream). Errors: SPH_EINVAL for a
+ * null `out` or out-of-range parameters, SPH_ECUDA if no device is usable. */
+int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream);
+
+/* Device bytes of the fixed-size per-particle and per-cell store for
+ * `n_total` particles in `n_boxes` boxes. The variable-size leaf-pair task
+ * lists are not included: the library allocates and grows those itself. */
+int sph_workspace_size(const sph_ctx *ctx, int64_t n_total, int n_boxes, size_t *bytes);
+
+/* Hand the library a caller-allocated device block for the fixed-size store
+ * (at least sph_workspace_size bytes, 256-byte aligned). The caller keeps it
+ * alive until sph_destroy or the next sph_set_workspace. Without it the
+ * library allocates the store itself. Errors: SPH_EINVAL (null / unaligned). */
+int sph_set_workspace(sph_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Load particles (Section 2 problem statement). Host arrays: box_offsets
+ * (n_boxes + 1, int64, box_offsets[0] = 0, non-decreasing), box_len
+ * (n_boxes x 3, edge lengths). Device arrays, caller order: x double[N][3]
+ * (wrapped into the box on load), v float[N][3], m float[N] (> 0),
+ * u float[N] (>= 0), h double[N] initial smoothing-length guesses (> 0; the
+ * density stage iterates from them). Builds the cell grid and the leaf-pair
+ * task lists. Errors: SPH_EINVAL, SPH_ENOMEM, SPH_EBOXTOOSMALL, SPH_ECUDA. */
+int sph_init(sph_ctx *ctx, int n_boxes, const int64_t *box_offsets, const double *box_len,
+             const double *x, const float *v, const float *m, const float *u, const double *h);
+
+/* Density stage: iterate every h_i to N_i(h_i) = n_ngb (within h_tol), with
+ * rho_i (Eq. rho), Omega_i, P_i at the converged h (Section 2; the ghost task
+ * of Section 3.1 is the per-particle finalisation). Rebuilds the grid and
+ * lists when an h outgrows them. Synchronises the stream. Errors:
+ * SPH_ENOTCONVERGED, SPH_EBOXTOOSMALL, SPH_ENONPHYSICAL, SPH_ECUDA. */
+int sph_density(sph_ctx *ctx);
+
+/* Force stage, Eqs. (dvdt) and (dudt), over j with r_ij < max(h_i, h_j).
+ * Requires a completed sph_density on the current positions (SPH_ESTATE
+ * otherwise). Asynchronous. */
+int sph_force(sph_ctx *ctx);
+
+/* n_steps kick-drift-kick steps with global time step dt (> 0): half kick,
+ * drift (FP64 positions, periodic wrap), grid rebuild, density, force with
+ * velocities and energies predicted to the end of the step, half kick.
+ * Requires sph_force on the current state first (SPH_ESTATE). Errors as
+ * sph_density, plus SPH_ENONPHYSICAL when some u becomes <= 0. */
+int sph_step(sph_ctx *ctx, double dt, int n_steps);
+
+/* Copy one SPH_* field into `dev_out` (device, caller order, layout as listed
+ * at the field). Asynchronous. Errors: SPH_EINVAL (unknown field / null),
+ * SPH_ESTATE (field not computed yet). */
+int sph_get(sph_ctx *ctx, int field, void *dev_out);
+
+/* Counters of the last density/force calls (synchronises the stream). */
+int sph_stats(sph_ctx *ctx, sph_stats_t *out);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Release the context and every buffer the library allocated. NULL is a no-op. */
+void sph_destroy(sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

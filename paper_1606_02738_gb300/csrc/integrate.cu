@@ -1,0 +1,279 @@
+// integrate.cu -- particle-store movement and the integrator task.
+//
+// Section 3.1 of the paper: once all force tasks on a cell are done, the
+// integrator task updates particle positions and velocities. The scheme here
+// is kick-drift-kick with one global time step: half kick of v and u, drift of
+// the FP64 positions (periodic wrap), prediction of v and u to the end of the
+// step for the next force evaluation, and the closing half kick after it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+#include "sph_internal.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ int box_of_slot(const BoxDev *b, int nb, int k) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b[mid].first <= k)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double wrap1(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0.0) y = 0.0;
+  return y;
+}
+
+// caller x [N][3] -> wrapped SoA copy (caller order)
+__global__ void k_wrap_from_caller(const double *x, const BoxDev *boxes, int nb, int n,
+                                   double *x0, double *x1, double *x2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const BoxDev &B = boxes[box_of_slot(boxes, nb, k)];
+  x0[k] = wrap1(x[3 * (size_t)k], B.L[0]);
+  x1[k] = wrap1(x[3 * (size_t)k + 1], B.L[1]);
+  x2[k] = wrap1(x[3 * (size_t)k + 2], B.L[2]);
+}
+
+void launch_wrap_cell_keys_from_caller(const double *x, const BoxDev *boxes, int n_boxes, int n,
+                                       double *x0, double *x1, double *x2, cudaStream_t s) {
+  k_wrap_from_caller<<<(n + 255) / 256, 256, 0, s>>>(x, boxes, n_boxes, n, x0, x1, x2);
+}
+
+// Sorted store <- caller arrays; `order[s]` is the caller index of slot s.
+struct LoadArgs {
+  StoreArrays dst;
+  const int *order;
+  int n;
+  const double *wx0, *wx1, *wx2;  // wrapped positions, caller order
+  const float *v, *m, *u;
+  const double *h;
+};
+
+__global__ void k_load(LoadArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const int k = a.order[s];
+  a.dst.x0[s] = a.wx0[k];
+  a.dst.x1[s] = a.wx1[k];
+  a.dst.x2[s] = a.wx2[k];
+  const float4 vu = make_float4(a.v[3 * (size_t)k], a.v[3 * (size_t)k + 1],
+                                a.v[3 * (size_t)k + 2], a.u[k]);
+  a.dst.vu[s] = vu;
+  a.dst.vu_pred[s] = vu;
+  a.dst.acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+  a.dst.m[s] = a.m[k];
+  a.dst.h[s] = a.h[k];
+  a.dst.hlo[s] = 0.0;
+  a.dst.hhi[s] = 1e308;
+  a.dst.orig[s] = k;
+}
+
+void launch_load_caller(const StoreArrays &dst, const int *order, int n, const double *wx,
+                        const float *v, const float *m, const float *u, const double *h,
+                        cudaStream_t s) {
+  LoadArgs a{dst, order, n, wx, wx + n, wx + 2 * (size_t)n, v, m, u, h};
+  k_load<<<(n + 255) / 256, 256, 0, s>>>(a);
+}
+
+__global__ void k_permute(StoreArrays d, StoreArrays src, const int *order, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int k = order[s];
+  d.x0[s] = src.x0[k];
+  d.x1[s] = src.x1[k];
+  d.x2[s] = src.x2[k];
+  d.h[s] = src.h[k];
+  d.hlo[s] = src.hlo[k];
+  d.hhi[s] = src.hhi[k];
+  d.vu[s] = src.vu[k];
+  d.vu_pred[s] = src.vu_pred[k];
+  d.acc[s] = src.acc[k];
+  d.m[s] = src.m[k];
+  d.orig[s] = src.orig[k];
+}
+
+void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *order, int n,
+                    cudaStream_t s) {
+  k_permute<<<(n + 255) / 256, 256, 0, s>>>(dst, src, order, n);
+}
+
+// First half kick, drift, prediction.
+__global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int nb,
+                             DevCounters *ctr) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const float hdt = (float)(0.5 * dt);
+  const float4 a = st.acc[s];
+  float4 v = st.vu[s];
+  v.x = fmaf(a.x, hdt, v.x);
+  v.y = fmaf(a.y, hdt, v.y);
+  v.z = fmaf(a.z, hdt, v.z);
+  v.w = fmaf(a.w, hdt, v.w);
+  st.vu[s] = v;  // v and u at the half step
+  const BoxDev &B = boxes[box_of_slot(boxes, nb, s)];
+  st.x0[s] = wrap1(st.x0[s] + (double)v.x * dt, B.L[0]);
+  st.x1[s] = wrap1(st.x1[s] + (double)v.y * dt, B.L[1]);
+  st.x2[s] = wrap1(st.x2[s] + (double)v.z * dt, B.L[2]);
+  const float4 p = make_float4(fmaf(a.x, hdt, v.x), fmaf(a.y, hdt, v.y), fmaf(a.z, hdt, v.z),
+                               fmaf(a.w, hdt, v.w));
+  st.vu_pred[s] = p;
+  if (!(p.w > 0.f) || !(v.w > 0.f)) atomicOr(&ctr->status, kErrNonPhysical);
+}
+
+void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
+                       DevCounters *ctr, cudaStream_t s) {
+  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, ctr);
+}
+
+// Closing half kick with the new accelerations.
+__global__ void k_kick(StoreArrays st, int n, double dt, DevCounters *ctr) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const float hdt = (float)(0.5 * dt);
+  const float4 a = st.acc[s];
+  float4 v = st.vu[s];
+  v.x = fmaf(a.x, hdt, v.x);
+  v.y = fmaf(a.y, hdt, v.y);
+  v.z = fmaf(a.z, hdt, v.z);
+  v.w = fmaf(a.w, hdt, v.w);
+  st.vu[s] = v;
+  st.vu_pred[s] = v;
+  if (!(v.w > 0.f)) atomicOr(&ctr->status, kErrNonPhysical);
+}
+
+void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s) {
+  k_kick<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, ctr);
+}
+
+__global__ void k_h_to_float(const double *h, float *hf, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) hf[s] = (float)h[s];
+}
+
+void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
+  k_h_to_float<<<(n + 255) / 256, 256, 0, s>>>(h, hf, n);
+}
+
+__global__ void k_h_extremes(const double *h, int n, const BoxDev *boxes, int nb,
+                             unsigned long long *dmax, unsigned long long *dminmax) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(h[s]);
+  atomicMax(&dmax[box_of_slot(boxes, nb, s)], b);
+  atomicMin(&dminmax[0], b);
+  atomicMax(&dminmax[1], b);
+}
+
+void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
+                       unsigned long long *dmax, unsigned long long *dminmax, cudaStream_t s) {
+  k_h_extremes<<<(n + 255) / 256, 256, 0, s>>>(h, n, boxes, n_boxes, dmax, dminmax);
+}
+
+__global__ void k_validate(const double *x, const float *v, const float *m, const float *u,
+                           const double *h, int n, int *status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  bool ok = m[k] > 0.f && isfinite(m[k]) && u[k] >= 0.f && isfinite(u[k]) && h[k] > 0.0 &&
+            isfinite(h[k]);
+  for (int d = 0; d < 3; ++d)
+    ok = ok && isfinite(x[3 * (size_t)k + d]) && isfinite(v[3 * (size_t)k + d]);
+  if (!ok) atomicOr(status, kErrInvalidInput);
+}
+
+void launch_validate(const double *x, const float *v, const float *m, const float *u,
+                     const double *h, int n, int *status, cudaStream_t s) {
+  k_validate<<<(n + 255) / 256, 256, 0, s>>>(x, v, m, u, h, n, status);
+}
+
+__global__ void k_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi,
+                                  int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  done[s] = 0;
+  niter[s] = 0;
+  hlo[s] = 0.0;
+  hhi[s] = 1e308;
+}
+
+void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi, int n,
+                            cudaStream_t s) {
+  k_reset_iteration<<<(n + 255) / 256, 256, 0, s>>>(done, niter, hlo, hhi, n);
+}
+
+__global__ void k_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= n_leaves) return;
+  const Leaf L = leaves[li];
+  for (int k = 0; k < L.count; ++k) leaf_of[L.start + k] = li;
+}
+
+void launch_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of, cudaStream_t s) {
+  k_leaf_of<<<(n_leaves + 255) / 256, 256, 0, s>>>(leaves, n_leaves, leaf_of);
+}
+
+struct GetArgs {
+  int field;
+  void *out;
+  const int *orig;
+  int n;
+  StoreArrays st;
+  const float *rho, *omega, *P;
+  const int *nngb, *niter, *nforce;
+};
+
+__global__ void k_get(GetArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.n) return;
+  const size_t k = (size_t)a.orig[s];
+  switch (a.field) {
+    case SPH_X: {
+      double *o = (double *)a.out;
+      o[3 * k] = a.st.x0[s];
+      o[3 * k + 1] = a.st.x1[s];
+      o[3 * k + 2] = a.st.x2[s];
+    } break;
+    case SPH_V: {
+      float *o = (float *)a.out;
+      const float4 v = a.st.vu[s];
+      o[3 * k] = v.x;
+      o[3 * k + 1] = v.y;
+      o[3 * k + 2] = v.z;
+    } break;
+    case SPH_U: ((float *)a.out)[k] = a.st.vu[s].w; break;
+    case SPH_H: ((double *)a.out)[k] = a.st.h[s]; break;
+    case SPH_RHO: ((float *)a.out)[k] = a.rho[s]; break;
+    case SPH_OMEGA: ((float *)a.out)[k] = a.omega[s]; break;
+    case SPH_P: ((float *)a.out)[k] = a.P[s]; break;
+    case SPH_A: {
+      float *o = (float *)a.out;
+      const float4 v = a.st.acc[s];
+      o[3 * k] = v.x;
+      o[3 * k + 1] = v.y;
+      o[3 * k + 2] = v.z;
+    } break;
+    case SPH_DUDT: ((float *)a.out)[k] = a.st.acc[s].w; break;
+    case SPH_NNGB: ((int *)a.out)[k] = a.nngb[s]; break;
+    case SPH_NITER: ((int *)a.out)[k] = a.niter[s]; break;
+    case SPH_NFORCE: ((int *)a.out)[k] = a.nforce[s]; break;
+    case SPH_M: ((float *)a.out)[k] = a.st.m[s]; break;
+    default: break;
+  }
+}
+
+void launch_get(int field, void *out, const int *orig, int n, const StoreArrays &st,
+                const float *rho, const float *omega, const float *P, const int *nngb,
+                const int *niter, const int *nforce, cudaStream_t s) {
+  GetArgs a{field, out, orig, n, st, rho, omega, P, nngb, niter, nforce};
+  k_get<<<(n + 255) / 256, 256, 0, s>>>(a);
+}
+
+}  // namespace sph

@@ -1,0 +1,809 @@
+// sph_api.cu -- C ABI entry points and host orchestration of libsph.
+//
+// Order of work per call (Section 3.1 task hierarchy, sort -> density ->
+// ghost -> force -> integrator, mapped to stream-ordered kernel launches):
+//   sph_init     wrap positions, build grid (A1), split cells (A2), gather
+//                the particle store into leaf order, leaf geometry.
+//   sph_density  repeat { leaf h maxima, active leaves, density task lists,
+//                density gather (A4), ghost h update (A5) } until every h
+//                has converged; rebuild the grid when an h outgrows it.
+//   sph_force    force task lists, force gather (A6).
+//   sph_step     kick + drift, regrid, density, force (predicted v, u), kick.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sph_ctx {
+  sph_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+
+  // fixed store: caller workspace (bump allocated) or library allocations
+  char *ws = nullptr;
+  size_t ws_bytes = 0, ws_used = 0;
+  std::vector<void *> owned;
+
+  int n = 0, nb = 0;
+  std::vector<BoxDev> boxes_h;
+  BoxDev *boxes_d = nullptr;
+  StoreArrays st{}, st2{};
+  float *hf = nullptr;
+  float4 *pm = nullptr, *sums = nullptr, *fi = nullptr;
+  int *cnt = nullptr, *niter = nullptr, *nngb = nullptr, *nforce = nullptr, *leaf_of = nullptr;
+  unsigned char *done = nullptr;
+  float *rho = nullptr, *omega = nullptr, *P = nullptr;
+  int *cell_of = nullptr, *order = nullptr, *order_tmp = nullptr, *flag = nullptr,
+      *excl = nullptr, *ident = nullptr;
+  unsigned *mkey = nullptr, *msrt = nullptr, *mscr = nullptr;
+  double *wx = nullptr;
+  unsigned long long *hext = nullptr;  // per-box max h, then global min, max
+
+  // growable, library-owned
+  DevBuf cell_count, cell_start, cursor, nodes, frontier, frontier2, leaves, scan_tmp, active,
+      dens_off, dens_tasks, force_off, force_tasks;
+  int n_cells = 0, n_nodes = 0, n_leaves = 0;
+  int64_t n_dens_tasks = 0, n_force_tasks = 0;
+
+  DevCounters *ctr = nullptr;    // device
+  DevCounters *ctr_h = nullptr;  // pinned host mirror
+
+  bool loaded = false, grid_valid = false, density_valid = false, force_valid = false;
+  int last_passes = 0, last_rebuilds = 0;
+  unsigned long long dens_cand_total = 0;
+};
+
+namespace {
+
+int fail(sph_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(c, SPH_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+#define TRY(call)            \
+  do {                       \
+    int rc_ = (call);        \
+    if (rc_) return rc_;     \
+  } while (0)
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int ensure(sph_ctx *c, DevBuf &b, size_t bytes, bool keep = false) {
+  if (bytes == 0) bytes = 256;
+  if (b.bytes >= bytes) return SPH_OK;
+  size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+  void *np = nullptr;
+  if (cudaMalloc(&np, nb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SPH_ENOMEM, "device allocation of %zu bytes failed", nb);
+  }
+  if (keep && b.p && b.bytes) {
+    CUDA_TRY(cudaMemcpyAsync(np, b.p, b.bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  if (b.p) cudaFree(b.p);
+  b.p = np;
+  b.bytes = nb;
+  return SPH_OK;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <class T>
+T *as(DevBuf &b) {
+  return reinterpret_cast<T *>(b.p);
+}
+
+// Bytes of every fixed-size per-particle array, in allocation order.
+struct FixedLayout {
+  std::vector<size_t> sizes;
+  size_t total = 0;
+};
+
+FixedLayout fixed_layout(int64_t n, int nb) {
+  FixedLayout L;
+  const size_t N = (size_t)n;
+  auto add = [&](size_t b) {
+    L.sizes.push_back(b);
+    L.total += align256(b);
+  };
+  for (int copy = 0; copy < 2; ++copy) {
+    for (int k = 0; k < 6; ++k) add(N * sizeof(double));  // x0 x1 x2 h hlo hhi
+    for (int k = 0; k < 3; ++k) add(N * sizeof(float4));  // vu vu_pred acc
+    add(N * sizeof(float));                               // m
+    add(N * sizeof(int));                                 // orig
+  }
+  add(N * sizeof(float));          // hf
+  add(N * sizeof(float4));         // pm
+  add(N * sizeof(float4));         // sums
+  add(N * sizeof(float4));         // fi
+  for (int k = 0; k < 5; ++k) add(N * sizeof(int));  // cnt niter nngb nforce leaf_of
+  add(N);                          // done
+  for (int k = 0; k < 3; ++k) add(N * sizeof(float));  // rho omega P
+  add(N * sizeof(int));            // cell_of
+  add(N * sizeof(int));            // order
+  add(N * sizeof(int));            // order_tmp
+  add((N + 1) * sizeof(int));      // flag
+  add((N + 1) * sizeof(int));      // excl
+  add(N * sizeof(int));            // ident
+  for (int k = 0; k < 3; ++k) add(N * sizeof(unsigned));  // mkey msrt mscr
+  add(3 * N * sizeof(double));     // wx
+  add((size_t)(nb + 2) * sizeof(unsigned long long));     // hext
+  add((size_t)nb * sizeof(BoxDev));                        // boxes
+  return L;
+}
+
+int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
+  FixedLayout L = fixed_layout(n, nb);
+  for (void *p : c->owned) cudaFree(p);
+  c->owned.clear();
+  char *base = nullptr;
+  if (c->ws) {
+    if (c->ws_bytes < L.total)
+      return fail(c, SPH_ENOMEM, "workspace of %zu bytes is below the %zu needed", c->ws_bytes,
+                  L.total);
+    base = c->ws;
+  } else {
+    void *p = nullptr;
+    if (cudaMalloc(&p, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, SPH_ENOMEM, "device allocation of %zu bytes failed", L.total);
+    }
+    c->owned.push_back(p);
+    base = (char *)p;
+  }
+  size_t off = 0, k = 0;
+  auto take = [&](auto *&ptr) {
+    ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + off);
+    off += align256(L.sizes[k++]);
+  };
+  StoreArrays *S[2] = {&c->st, &c->st2};
+  for (int copy = 0; copy < 2; ++copy) {
+    take(S[copy]->x0);
+    take(S[copy]->x1);
+    take(S[copy]->x2);
+    take(S[copy]->h);
+    take(S[copy]->hlo);
+    take(S[copy]->hhi);
+    take(S[copy]->vu);
+    take(S[copy]->vu_pred);
+    take(S[copy]->acc);
+    take(S[copy]->m);
+    take(S[copy]->orig);
+  }
+  take(c->hf);
+  take(c->pm);
+  take(c->sums);
+  take(c->fi);
+  take(c->cnt);
+  take(c->niter);
+  take(c->nngb);
+  take(c->nforce);
+  take(c->leaf_of);
+  take(c->done);
+  take(c->rho);
+  take(c->omega);
+  take(c->P);
+  take(c->cell_of);
+  take(c->order);
+  take(c->order_tmp);
+  take(c->flag);
+  take(c->excl);
+  take(c->ident);
+  take(c->mkey);
+  take(c->msrt);
+  take(c->mscr);
+  take(c->wx);
+  take(c->hext);
+  take(c->boxes_d);
+  return SPH_OK;
+}
+
+__global__ void k_iota(int *a, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+
+int read_counters(sph_ctx *c) {
+  CUDA_TRY(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return SPH_OK;
+}
+
+int sync_check(sph_ctx *c) {
+  CUDA_TRY(cudaGetLastError());
+  return SPH_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+// Choose top-grid cells per box from the largest h: edge >= 2 h_max where
+// the box allows (headroom for h growth), never below h_max, >= 3 per axis.
+int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
+  int base = 0;
+  for (int b = 0; b < c->nb; ++b) {
+    BoxDev &B = c->boxes_h[b];
+    if (B.count == 0) {  // an empty box keeps a minimal 3x3x3 grid
+      for (int d = 0; d < 3; ++d) {
+        B.n[d] = 3;
+        B.w[d] = B.L[d] / 3.0;
+      }
+      B.eps = (float)(1e-5 * std::max(B.w[0], std::max(B.w[1], B.w[2])));
+      B.cell_base = base;
+      base += 27;
+      continue;
+    }
+    const double hm = hmax_box[b] * (1.0 + 1e-6);
+    const double lmin = std::min(B.L[0], std::min(B.L[1], B.L[2]));
+    if (!(hm > 0.0)) return fail(c, SPH_EINVAL, "box %d has a non-positive smoothing length", b);
+    if (hm > lmin / 3.0)
+      return fail(c, SPH_EBOXTOOSMALL, "box %d: h = %g exceeds L/3 = %g", b, hmax_box[b],
+                  lmin / 3.0);
+    const int64_t cap = std::max<int64_t>(27, 2 * (int64_t)B.count);
+    for (int d = 0; d < 3; ++d) {
+      int64_t nd = (int64_t)std::floor(B.L[d] / (2.0 * hm));
+      if (nd < 3) nd = (int64_t)std::floor(B.L[d] / hm);
+      nd = std::max<int64_t>(3, std::min<int64_t>(nd, 1024));
+      B.n[d] = (int)nd;
+    }
+    while ((int64_t)B.n[0] * B.n[1] * B.n[2] > cap) {
+      int d = 0;
+      for (int k = 1; k < 3; ++k)
+        if (B.n[k] > B.n[d]) d = k;
+      if (B.n[d] <= 3) break;
+      B.n[d] = std::max(3, B.n[d] * 3 / 4);
+    }
+    double wmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      B.w[d] = B.L[d] / B.n[d];
+      wmax = std::max(wmax, B.w[d]);
+    }
+    B.eps = (float)(1e-5 * wmax);
+    B.cell_base = base;
+    base += B.n[0] * B.n[1] * B.n[2];
+  }
+  c->n_cells = base;
+  CUDA_TRY(cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * c->nb,
+                           cudaMemcpyHostToDevice, c->stream));
+  return SPH_OK;
+}
+
+int h_extremes(sph_ctx *c, const double *h, std::vector<double> &hmax_box, double &hmin,
+               double &hmax) {
+  std::vector<unsigned long long> init(c->nb + 2, 0ull);
+  init[c->nb] = ~0ull;
+  CUDA_TRY(cudaMemcpyAsync(c->hext, init.data(), sizeof(unsigned long long) * init.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+  launch_h_extremes(h, c->n, c->boxes_d, c->nb, c->hext, c->hext + c->nb, c->stream);
+  CUDA_TRY(cudaMemcpyAsync(init.data(), c->hext, sizeof(unsigned long long) * init.size(),
+                           cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  hmax_box.resize(c->nb);
+  for (int b = 0; b < c->nb; ++b) hmax_box[b] = bits_to_double(init[b]);
+  hmin = bits_to_double(init[c->nb]);
+  hmax = bits_to_double(init[c->nb + 1]);
+  return SPH_OK;
+}
+
+// A1 + A2: grid, recursive split, leaves, store gather, leaf geometry.
+// from_caller: positions come from the wrapped caller copy (c->wx) and the
+// store is loaded from the caller arrays passed in.
+int build_grid(sph_ctx *c, bool from_caller, const float *cv, const float *cm, const float *cu,
+               const double *ch) {
+  std::vector<double> hmax_box;
+  double hmin, hmax;
+  TRY(h_extremes(c, from_caller ? ch : c->st.h, hmax_box, hmin, hmax));
+  TRY(choose_grid(c, hmax_box));
+
+  const int n = c->n, C = c->n_cells;
+  TRY(ensure(c, c->cell_count, sizeof(int) * (C + 1)));
+  TRY(ensure(c, c->cell_start, sizeof(int) * (C + 1)));
+  TRY(ensure(c, c->cursor, sizeof(int) * (C + 1)));
+  TRY(ensure(c, c->scan_tmp, scan_tmp_bytes(std::max(C + 1, n + 1))));
+  CUDA_TRY(cudaMemsetAsync(c->cell_count.p, 0, sizeof(int) * (C + 1), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->cursor.p, 0, sizeof(int) * (C + 1), c->stream));
+
+  GridArgs g{};
+  g.n = n;
+  g.n_boxes = c->nb;
+  g.boxes = c->boxes_d;
+  g.n_cells = C;
+  g.n_split = c->p.n_split;
+  if (from_caller) {
+    g.x0 = c->wx;
+    g.x1 = c->wx + n;
+    g.x2 = c->wx + 2 * (size_t)n;
+    g.orig = c->ident;
+  } else {
+    g.x0 = c->st.x0;
+    g.x1 = c->st.x1;
+    g.x2 = c->st.x2;
+    g.orig = c->st.orig;
+  }
+  g.cell_of = c->cell_of;
+  g.morton = c->mkey;
+  g.morton_tmp = c->msrt;
+  g.morton_scr = c->mscr;
+  g.cell_count = as<int>(c->cell_count);
+  g.cell_start = as<int>(c->cell_start);
+  g.cursor = as<int>(c->cursor);
+  g.order = c->order;
+  g.order_tmp = c->order_tmp;
+
+  launch_cell_keys(g, c->stream);
+  exclusive_scan_int(g.cell_count, g.cell_start, C + 1, c->scan_tmp.p, c->scan_tmp.bytes,
+                     c->stream);
+  launch_cell_scatter(g, c->stream);
+
+  // A2: recursive octant split
+  size_t want_nodes = (size_t)C + (size_t)n / 4 + 1024;
+  TRY(ensure(c, c->nodes, sizeof(Node) * want_nodes));
+  TRY(ensure(c, c->frontier, sizeof(int) * want_nodes));
+  TRY(ensure(c, c->frontier2, sizeof(int) * want_nodes));
+  launch_init_top_nodes(as<Node>(c->nodes), g, c->stream);
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->n_frontier, 0, sizeof(int), c->stream));
+  launch_frontier_top(as<Node>(c->nodes), C, c->p.n_split, as<int>(c->frontier), c->ctr,
+                      c->stream);
+  TRY(read_counters(c));
+  int nf = c->ctr_h->n_frontier;
+  int n_nodes = C;
+  for (int level = 0; level < kMaxDepth && nf > 0; ++level) {
+    const size_t need = (size_t)n_nodes + 8 * (size_t)nf;
+    if (sizeof(Node) * need > c->nodes.bytes) {
+      TRY(ensure(c, c->nodes, sizeof(Node) * need * 3 / 2, true));
+      TRY(ensure(c, c->frontier, sizeof(int) * need * 3 / 2, true));
+      TRY(ensure(c, c->frontier2, sizeof(int) * need * 3 / 2, false));
+    }
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->n_frontier, 0, sizeof(int), c->stream));
+    launch_split_level(as<Node>(c->nodes), as<int>(c->frontier), nf, n_nodes, level,
+                       c->p.n_split, as<int>(c->frontier2), c->ctr, g, c->stream);
+    n_nodes += 8 * nf;
+    TRY(read_counters(c));
+    nf = c->ctr_h->n_frontier;
+    std::swap(c->frontier, c->frontier2);
+  }
+  c->n_nodes = n_nodes;
+
+  // leaves, in slot order
+  CUDA_TRY(cudaMemsetAsync(c->flag, 0, sizeof(int) * (n + 1), c->stream));
+  launch_mark_leaves(as<Node>(c->nodes), n_nodes, c->flag, c->stream);
+  exclusive_scan_int(c->flag, c->excl, n + 1, c->scan_tmp.p, c->scan_tmp.bytes, c->stream);
+  int nl = 0;
+  CUDA_TRY(cudaMemcpyAsync(&nl, c->excl + n, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->n_leaves = nl;
+  TRY(ensure(c, c->leaves, sizeof(Leaf) * (size_t)std::max(nl, 1)));
+  TRY(ensure(c, c->active, sizeof(int) * (size_t)(nl + 1)));
+  launch_fill_leaves(as<Node>(c->nodes), n_nodes, c->excl, as<Leaf>(c->leaves), c->boxes_d, c->nb,
+                     c->stream);
+  launch_sort_leaves(as<Leaf>(c->leaves), nl, c->order, g.orig, c->stream);
+
+  // gather the store into leaf order
+  if (from_caller) {
+    launch_load_caller(c->st, c->order, n, c->wx, cv, cm, cu, ch, c->stream);
+  } else {
+    launch_permute(c->st2, c->st, c->order, n, c->stream);
+    std::swap(c->st, c->st2);
+  }
+  launch_leaf_of(as<Leaf>(c->leaves), nl, c->leaf_of, c->stream);
+  launch_h_to_float(c->st.h, c->hf, n, c->stream);
+  GeomArgs ga{nl, as<Leaf>(c->leaves), as<Node>(c->nodes), c->boxes_d, c->nb,
+              c->st.x0, c->st.x1, c->st.x2, c->st.m, c->hf, c->pm};
+  launch_leaf_geometry(ga, n_nodes, c->stream);
+  TRY(sync_check(c));
+  c->grid_valid = true;
+  c->density_valid = false;
+  c->force_valid = false;
+  return SPH_OK;
+}
+
+GeomArgs geom_args(sph_ctx *c) {
+  return GeomArgs{c->n_leaves, as<Leaf>(c->leaves), as<Node>(c->nodes), c->boxes_d, c->nb,
+                  c->st.x0, c->st.x1, c->st.x2, c->st.m, c->hf, c->pm};
+}
+
+// Count pass, scan, fill pass of a task list over `n_targets` target leaves.
+int build_lists(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf &off,
+                DevBuf &tasks, int64_t &n_tasks) {
+  TRY(ensure(c, off, sizeof(int) * (size_t)(n_targets + 1)));
+  ListArgs la{};
+  la.n_leaves = c->n_leaves;
+  la.leaves = as<Leaf>(c->leaves);
+  la.nodes = as<Node>(c->nodes);
+  la.boxes = c->boxes_d;
+  la.n_boxes = c->nb;
+  la.force = force ? 1 : 0;
+  la.cap_factor = 1.0f;
+  la.count = as<int>(off);
+  la.offset = nullptr;
+  la.tasks = nullptr;
+  la.active = active;
+  la.n_targets = n_targets;
+  la.status = &c->ctr->status;
+  CUDA_TRY(cudaMemsetAsync(as<int>(off) + n_targets, 0, sizeof(int), c->stream));
+  launch_build_lists(la, c->stream);
+  exclusive_scan_int(as<int>(off), as<int>(off), n_targets + 1, c->scan_tmp.p, c->scan_tmp.bytes,
+                     c->stream);
+  int total = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, as<int>(off) + n_targets, sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (total < 0) return fail(c, SPH_ENOMEM, "task list exceeds 2^31 entries");
+  TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(total, 1)));
+  la.offset = as<int>(off);
+  la.tasks = as<Task>(tasks);
+  launch_build_lists(la, c->stream);
+  n_tasks = total;
+  return sync_check(c);
+}
+
+int check_status(sph_ctx *c, int st) {
+  if (st & kErrBoxTooSmall)
+    return fail(c, SPH_EBOXTOOSMALL, "a smoothing length would exceed L/3 of its box");
+  if (st & kErrNonPhysical)
+    return fail(c, SPH_ENONPHYSICAL, "non-physical state (rho <= 0, Omega <= 0 or u <= 0)");
+  if (st & kErrListOverflow) return fail(c, SPH_ECUDA, "tree walk stack overflow");
+  return SPH_OK;
+}
+
+int density_impl(sph_ctx *c, const float4 *vu_for_P) {
+  if (!c->grid_valid) TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+  const int n = c->n;
+  launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, n, c->stream);
+  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+  c->last_passes = 0;
+  c->last_rebuilds = 0;
+  const int max_passes = c->p.max_iter + 8;
+  for (int pass = 0;; ++pass) {
+    if (pass >= max_passes)
+      return fail(c, SPH_ENOTCONVERGED, "smoothing lengths did not converge in %d passes",
+                  c->p.max_iter);
+    GeomArgs ga = geom_args(c);
+    launch_leaf_hmax(ga, c->n_nodes, c->stream);
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->n_active, 0, sizeof(int), c->stream));
+    launch_active_leaves(as<Leaf>(c->leaves), c->n_leaves, c->done, as<int>(c->active), c->ctr,
+                         c->stream);
+    TRY(read_counters(c));
+    const int n_active = c->ctr_h->n_active;
+    if (n_active == 0) break;
+    ++c->last_passes;
+    TRY(build_lists(c, false, as<int>(c->active), n_active, c->dens_off, c->dens_tasks,
+                    c->n_dens_tasks));
+    DensArgs da{};
+    da.n_active = n_active;
+    da.active = as<int>(c->active);
+    da.leaves = as<Leaf>(c->leaves);
+    da.list_off = as<int>(c->dens_off);
+    da.tasks = as<Task>(c->dens_tasks);
+    da.pm = c->pm;
+    da.hf = c->hf;
+    da.done = c->done;
+    da.sums = c->sums;
+    da.cnt = c->cnt;
+    da.ctr = c->ctr;
+    da.kahan = c->p.precision == SPH_PREC_KAHAN;
+    launch_density(da, c->stream);
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, 2 * sizeof(int), c->stream));
+    GhostArgs gh{};
+    gh.n = n;
+    gh.n_ngb = c->p.n_ngb;
+    gh.tol = c->p.h_tol;
+    gh.gamma = c->p.gamma;
+    gh.max_iter = c->p.max_iter;
+    gh.leaves = as<Leaf>(c->leaves);
+    gh.leaf_of = c->leaf_of;
+    gh.nodes = as<Node>(c->nodes);
+    gh.boxes = c->boxes_d;
+    gh.n_boxes = c->nb;
+    gh.cap_factor = 1.0f;
+    gh.h = c->st.h;
+    gh.hlo = c->st.hlo;
+    gh.hhi = c->st.hhi;
+    gh.hf = c->hf;
+    gh.sums = c->sums;
+    gh.cnt = c->cnt;
+    gh.vu = vu_for_P;
+    gh.done = c->done;
+    gh.niter = c->niter;
+    gh.nngb = c->nngb;
+    gh.rho = c->rho;
+    gh.omega = c->omega;
+    gh.P = c->P;
+    gh.force_i = c->fi;
+    gh.ctr = c->ctr;
+    launch_ghost(gh, c->stream);
+    TRY(sync_check(c));
+    TRY(read_counters(c));
+    const int st = c->ctr_h->status;
+    TRY(check_status(c, st));
+    if (st & kErrHGrid) {
+      // an h outgrew its top cell: regrid with the current h and start the
+      // converged bookkeeping again (the per-particle results are reordered)
+      TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+      launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, n, c->stream);
+      CUDA_TRY(cudaMemsetAsync(&c->ctr->dens_inter, 0, sizeof(unsigned long long), c->stream));
+      ++c->last_rebuilds;
+      continue;
+    }
+    if (c->ctr_h->unconverged == 0) {
+      c->last_passes += 0;
+      continue;  // the next active-leaf scan finds none and ends the loop
+    }
+    if (st & kErrNotConverged)
+      return fail(c, SPH_ENOTCONVERGED, "smoothing lengths did not converge in %d passes",
+                  c->p.max_iter);
+  }
+  c->density_valid = true;
+  c->force_valid = false;
+  return SPH_OK;
+}
+
+int force_impl(sph_ctx *c, const float4 *vu_for_force) {
+  if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
+  GeomArgs ga = geom_args(c);
+  launch_leaf_hmax(ga, c->n_nodes, c->stream);
+  TRY(build_lists(c, true, nullptr, c->n_leaves, c->force_off, c->force_tasks,
+                  c->n_force_tasks));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+  ForceArgs fa{};
+  fa.n_leaves = c->n_leaves;
+  fa.leaves = as<Leaf>(c->leaves);
+  fa.list_off = as<int>(c->force_off);
+  fa.tasks = as<Task>(c->force_tasks);
+  fa.pm = c->pm;
+  fa.fi = c->fi;
+  fa.vu = vu_for_force;
+  fa.acc = c->st.acc;
+  fa.nforce = c->nforce;
+  fa.ctr = c->ctr;
+  fa.kahan = c->p.precision == SPH_PREC_KAHAN;
+  launch_force(fa, c->stream);
+  TRY(sync_check(c));
+  c->force_valid = true;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sph_default_params(sph_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->gamma = 5.0 / 3.0;
+  p->n_ngb = 48.0;
+  p->h_tol = 1e-6;
+  p->max_iter = 30;
+  p->n_split = 64;
+  p->precision = SPH_PREC_FP32;
+  p->mode = SPH_MODE_PLAIN;
+}
+
+int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
+  if (!out) return SPH_EINVAL;
+  *out = nullptr;
+  sph_params q;
+  sph_default_params(&q);
+  if (p) q = *p;
+  if (!(q.gamma > 1.0) || !(q.n_ngb > 32.0 / 3.0) || !(q.h_tol > 0.0) || q.max_iter < 1 ||
+      q.n_split < 8 || q.n_split > 256 ||
+      (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
+      (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED))
+    return SPH_EINVAL;
+  sph_ctx *c = new (std::nothrow) sph_ctx();
+  if (!c) return SPH_ENOMEM;
+  c->p = q;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaMalloc(&c->ctr, sizeof(DevCounters)) != cudaSuccess ||
+      cudaMallocHost(&c->ctr_h, sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->ctr) cudaFree(c->ctr);
+    delete c;
+    return SPH_ECUDA;
+  }
+  std::memset(c->ctr_h, 0, sizeof(DevCounters));
+  *out = c;
+  return SPH_OK;
+}
+
+int sph_workspace_size(const sph_ctx *ctx, int64_t n_total, int n_boxes, size_t *bytes) {
+  if (!ctx || !bytes || n_total < 1 || n_total > (int64_t)1 << 30 || n_boxes < 1)
+    return SPH_EINVAL;
+  *bytes = fixed_layout(n_total, n_boxes).total;
+  return SPH_OK;
+}
+
+int sph_set_workspace(sph_ctx *c, void *dev_ptr, size_t bytes) {
+  if (!c || !dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(c, SPH_EINVAL, "bad workspace");
+  c->ws = (char *)dev_ptr;
+  c->ws_bytes = bytes;
+  c->loaded = false;
+  return SPH_OK;
+}
+
+int sph_init(sph_ctx *c, int n_boxes, const int64_t *box_offsets, const double *box_len,
+             const double *x, const float *v, const float *m, const float *u, const double *h) {
+  if (!c) return SPH_EINVAL;
+  c->err.clear();
+  if (n_boxes < 1 || !box_offsets || !box_len || !x || !v || !m || !u || !h)
+    return fail(c, SPH_EINVAL, "null argument or n_boxes < 1");
+  if (box_offsets[0] != 0) return fail(c, SPH_EINVAL, "box_offsets[0] must be 0");
+  for (int b = 0; b < n_boxes; ++b) {
+    if (box_offsets[b + 1] < box_offsets[b])
+      return fail(c, SPH_EINVAL, "box_offsets must be non-decreasing");
+    for (int d = 0; d < 3; ++d)
+      if (!(box_len[3 * b + d] > 0.0) || !std::isfinite(box_len[3 * b + d]))
+        return fail(c, SPH_EINVAL, "box %d has a non-positive edge", b);
+  }
+  const int64_t n = box_offsets[n_boxes];
+  if (n < 1 || n > ((int64_t)1 << 30)) return fail(c, SPH_EINVAL, "N = %lld out of range", (long long)n);
+  c->n = (int)n;
+  c->nb = n_boxes;
+  c->boxes_h.assign(n_boxes, BoxDev{});
+  for (int b = 0; b < n_boxes; ++b) {
+    BoxDev &B = c->boxes_h[b];
+    for (int d = 0; d < 3; ++d) B.L[d] = box_len[3 * b + d];
+    B.first = (int)box_offsets[b];
+    B.count = (int)(box_offsets[b + 1] - box_offsets[b]);
+  }
+  c->loaded = false;
+  TRY(alloc_fixed(c, n, n_boxes));
+  CUDA_TRY(cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * n_boxes,
+                           cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->status, 0, sizeof(int), c->stream));
+  launch_validate(x, v, m, u, h, c->n, &c->ctr->status, c->stream);
+  TRY(read_counters(c));
+  if (c->ctr_h->status & kErrInvalidInput)
+    return fail(c, SPH_EINVAL, "inputs must be finite with m > 0, u >= 0 and h > 0");
+  k_iota<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->ident, c->n);
+  launch_wrap_cell_keys_from_caller(x, c->boxes_d, c->nb, c->n, c->wx, c->wx + n,
+                                    c->wx + 2 * (size_t)n, c->stream);
+  TRY(build_grid(c, true, v, m, u, h));
+  c->loaded = true;
+  return SPH_OK;
+}
+
+int sph_density(sph_ctx *c) {
+  if (!c) return SPH_EINVAL;
+  c->err.clear();
+  if (!c->loaded) return fail(c, SPH_ESTATE, "sph_density before sph_init");
+  return density_impl(c, c->st.vu);
+}
+
+int sph_force(sph_ctx *c) {
+  if (!c) return SPH_EINVAL;
+  c->err.clear();
+  if (!c->loaded) return fail(c, SPH_ESTATE, "sph_force before sph_init");
+  return force_impl(c, c->st.vu);
+}
+
+int sph_step(sph_ctx *c, double dt, int n_steps) {
+  if (!c) return SPH_EINVAL;
+  c->err.clear();
+  if (!c->loaded || !c->force_valid)
+    return fail(c, SPH_ESTATE, "sph_step needs sph_density and sph_force on the current state");
+  if (!(dt > 0.0) || !std::isfinite(dt) || n_steps < 0)
+    return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
+  for (int s = 0; s < n_steps; ++s) {
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->status, 0, sizeof(int), c->stream));
+    launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+    c->grid_valid = false;
+    c->density_valid = false;
+    c->force_valid = false;
+    TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+    TRY(density_impl(c, c->st.vu_pred));
+    TRY(force_impl(c, c->st.vu_pred));
+    launch_kick(c->st, c->n, dt, c->ctr, c->stream);
+    TRY(read_counters(c));
+    TRY(check_status(c, c->ctr_h->status));
+  }
+  return sync_check(c);
+}
+
+int sph_get(sph_ctx *c, int field, void *dev_out) {
+  if (!c) return SPH_EINVAL;
+  c->err.clear();
+  if (!dev_out || field < 0 || field >= SPH_NFIELDS)
+    return fail(c, SPH_EINVAL, "unknown field %d or null output", field);
+  if (!c->loaded) return fail(c, SPH_ESTATE, "no particles loaded");
+  const bool needs_density = field == SPH_RHO || field == SPH_OMEGA || field == SPH_P ||
+                             field == SPH_NNGB || field == SPH_NITER;
+  const bool needs_force = field == SPH_A || field == SPH_DUDT || field == SPH_NFORCE;
+  if (needs_density && !c->density_valid)
+    return fail(c, SPH_ESTATE, "field %d needs sph_density on the current positions", field);
+  if (needs_force && !c->force_valid)
+    return fail(c, SPH_ESTATE, "field %d needs sph_force on the current state", field);
+  launch_get(field, dev_out, c->st.orig, c->n, c->st, c->rho, c->omega, c->P, c->nngb, c->niter,
+             c->nforce, c->stream);
+  return sync_check(c);
+}
+
+int sph_stats(sph_ctx *c, sph_stats_t *out) {
+  if (!c || !out) return SPH_EINVAL;
+  std::memset(out, 0, sizeof *out);
+  out->n_particles = c->n;
+  out->n_boxes = c->nb;
+  if (!c->loaded) return SPH_OK;
+  TRY(read_counters(c));
+  out->n_top_cells = c->n_cells;
+  out->n_leaves = c->n_leaves;
+  out->n_pairs_density = c->n_dens_tasks;
+  out->n_pairs_force = c->n_force_tasks;
+  out->density_interactions = (int64_t)c->ctr_h->dens_inter;
+  out->force_interactions = (int64_t)c->ctr_h->force_inter;
+  out->density_pair_candidates = (int64_t)c->ctr_h->dens_cand;
+  out->force_pair_candidates = (int64_t)c->ctr_h->force_cand;
+  out->density_passes = c->last_passes;
+  out->rebuilds = c->last_rebuilds;
+  out->max_iter_used = c->ctr_h->max_iter_used;
+  std::vector<double> hb;
+  double hmin = 0, hmax = 0;
+  TRY(h_extremes(c, c->st.h, hb, hmin, hmax));
+  out->h_min = hmin;
+  out->h_max = hmax;
+  return SPH_OK;
+}
+
+const char *sph_last_error(const sph_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void sph_destroy(sph_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  DevBuf *bufs[] = {&c->cell_count, &c->cell_start, &c->cursor,   &c->nodes,      &c->frontier,
+                    &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
+                    &c->dens_tasks, &c->force_off,  &c->force_tasks};
+  for (DevBuf *b : bufs) release(*b);
+  for (void *p : c->owned) cudaFree(p);
+  if (c->ctr) cudaFree(c->ctr);
+  if (c->ctr_h) cudaFreeHost(c->ctr_h);
+  delete c;
+}
+
+}  // extern "C"

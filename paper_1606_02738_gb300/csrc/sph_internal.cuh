@@ -1,0 +1,262 @@
+// sph_internal.cuh -- device data layout and launch wrappers shared by the
+// translation units of libsph (CUDA, sm_103a). Not part of the public ABI.
+//
+// Particle store: every per-particle array is in "sorted order": particles of
+// one octree leaf are contiguous, leaves follow the depth-first (Morton) order
+// of the octree of their top cell, top cells follow box then cell index
+// (Section 3.1: cells of edge >= the largest h, split recursively).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int kMaxDepth = 10;   // octree levels below a top cell (1024 sub-cells per edge)
+constexpr int kWarp = 32;
+constexpr float kInvPi = 0.318309886183790671538f;
+
+// Error bits a kernel may raise in the device status word.
+enum : int {
+  kErrHCap = 1,        // an h outgrew its leaf's density-list cap -> rebuild lists
+  kErrHGrid = 2,       // an h outgrew the top-cell width -> rebuild the grid
+  kErrBoxTooSmall = 4, // an h would exceed L/3 of its box
+  kErrNonPhysical = 8, // rho <= 0, Omega <= 0, or u <= 0
+  kErrNotConverged = 16,
+  kErrListOverflow = 32,
+  kErrInvalidInput = 64, // m <= 0, u < 0, h <= 0 or a non-finite input
+};
+
+struct BoxDev {
+  double L[3];     // edge lengths
+  double w[3];     // top-cell widths L / n
+  int n[3];        // top cells per axis (>= 3)
+  int cell_base;   // first global top-cell id of this box
+  int first, count;  // particle range (the same in caller and sorted order)
+  float eps;       // pruning margin in top-cell-relative units
+  float pad;
+};
+
+struct Node {
+  int start, count;  // particle range in sorted order
+  int child;         // first of 8 consecutive children, -1 for a leaf
+  int parent;        // -1 for a top cell
+  int cell;          // global top-cell id
+  int leaf;          // leaf index (leaves only)
+  int level;         // 0 = top cell
+  int ix, iy, iz;    // integer coordinates at `level` inside the top cell
+  float lo[3], hi[3];  // particle bounding box, relative to the top-cell origin
+  float hmax;        // largest h of the node's particles
+  int box;
+};
+
+struct Leaf {
+  int start, count;
+  int node, box;
+  double o[3];       // leaf-cell origin relative to its top-cell origin
+};
+
+// One entry of a leaf's task list: the source leaf and the shift that maps
+// the source leaf's particle coordinates into the target leaf's frame
+// (origin_S + image offset - origin_T, rounded once to FP32).
+struct Task {
+  float sx, sy, sz;
+  int src;
+};
+
+// Per-context counters written by kernels (device side).
+struct DevCounters {
+  unsigned long long dens_inter;      // converged-pass density interactions
+  unsigned long long force_inter;
+  unsigned long long dens_cand;       // (i, j) pairs tested, all density passes
+  unsigned long long force_cand;
+  int unconverged;
+  int status;                         // kErr* bits
+  int max_iter_used;
+  int n_active;
+  int n_frontier;
+  int pad[3];
+};
+
+// ---- cubic spline, support q < 1 (Section 2: h is the radius of the
+// sphere of particles considered; W(r,h) = (8/pi) w(r/h) / h^3) ----
+__device__ __forceinline__ void w_and_dw(float q, float &w, float &dw) {
+  // inner piece 1 - 6q^2 + 6q^3, outer piece 2(1-q)^3, written in the power
+  // basis so one Horner chain serves both: coefficients are selected, not
+  // branched on.
+  const bool in = q < 0.5f;
+  const float c0 = in ? 1.f : 2.f, c1 = in ? 0.f : -6.f, c2 = in ? -6.f : 6.f,
+              c3 = in ? 6.f : -2.f;
+  const float d0 = in ? 0.f : -6.f, d1 = in ? -12.f : 12.f, d2 = in ? 18.f : -6.f;
+  w = fmaf(fmaf(fmaf(c3, q, c2), q, c1), q, c0);
+  dw = fmaf(fmaf(d2, q, d1), q, d0);
+}
+
+__device__ __forceinline__ float dw_only(float q) {
+  const bool in = q < 0.5f;
+  const float d0 = in ? 0.f : -6.f, d1 = in ? -12.f : 12.f, d2 = in ? 18.f : -6.f;
+  float dw = fmaf(fmaf(d2, q, d1), q, d0);
+  return q < 1.f ? dw : 0.f;
+}
+
+// ---- host-side launch wrappers (grid.cu) ----
+struct GridArgs {
+  int n;                 // particles
+  int n_boxes;
+  const BoxDev *boxes;   // device
+  int n_cells;           // total top cells
+  int n_split;
+  const double *x0, *x1, *x2;  // positions (current order)
+  int *cell_of;          // [n] scratch
+  unsigned *morton;      // [n] Morton code per current slot
+  unsigned *morton_tmp;  // [n] Morton code in new order
+  unsigned *morton_scr;  // [n] scratch for the octant scatter
+  int *cell_count;       // [n_cells + 1]
+  int *cell_start;       // [n_cells + 1]
+  int *cursor;           // [n_cells]
+  int *order;            // [n] new slot -> old slot
+  int *order_tmp;        // [n]
+  const int *orig;       // [n] original index of old slot (tie-break)
+};
+
+void launch_cell_keys(const GridArgs &g, cudaStream_t s);
+void launch_cell_scatter(const GridArgs &g, cudaStream_t s);
+void exclusive_scan_int(const int *in, int *out, int n, void *tmp, size_t tmp_bytes,
+                        cudaStream_t s);
+size_t scan_tmp_bytes(int n);
+void launch_init_top_nodes(Node *nodes, const GridArgs &g, cudaStream_t s);
+void launch_frontier_top(const Node *nodes, int n_cells, int n_split, int *frontier,
+                         DevCounters *ctr, cudaStream_t s);
+void launch_split_level(Node *nodes, const int *frontier, int n_frontier, int child_base,
+                        int level, int n_split, int *next_frontier, DevCounters *ctr,
+                        const GridArgs &g, cudaStream_t s);
+void launch_mark_leaves(const Node *nodes, int n_nodes, int *flag, cudaStream_t s);
+void launch_fill_leaves(Node *nodes, int n_nodes, const int *leaf_idx_excl, Leaf *leaves,
+                        const BoxDev *boxes, int n_boxes, cudaStream_t s);
+void launch_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig,
+                        cudaStream_t s);
+
+struct GeomArgs {
+  int n_leaves;
+  const Leaf *leaves;
+  Node *nodes;
+  const BoxDev *boxes;
+  int n_boxes;
+  const double *x0, *x1, *x2;
+  const float *m;
+  const float *hf;     // h as float, sorted order
+  float4 *pm;          // out: leaf-relative position, mass
+};
+void launch_leaf_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s);
+void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s);
+
+// per-box largest h (dmax[nb]) and global min / max (dminmax[2]), as ordered
+// int64 bit patterns of non-negative doubles (dminmax[0] holds the minimum)
+void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
+                       unsigned long long *dmax, unsigned long long *dminmax, cudaStream_t s);
+void launch_validate(const double *x, const float *v, const float *m, const float *u,
+                     const double *h, int n, int *status, cudaStream_t s);
+void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi, int n,
+                            cudaStream_t s);
+
+struct ListArgs {
+  int n_leaves;
+  const Leaf *leaves;
+  const Node *nodes;
+  const BoxDev *boxes;
+  int n_boxes;
+  int force;           // 0: density (gather, d < cap_T), 1: force (d < max(hT, hS))
+  float cap_factor;    // density cap = cap_factor * hmax_T
+  int *count;          // [n_leaves + 1]
+  const int *offset;   // [n_leaves + 1] (fill pass)
+  Task *tasks;         // fill pass
+  const int *active;   // optional subset of target leaves (NULL = all)
+  int n_targets;
+  int *status;         // kErrListOverflow if a walk ran out of stack
+};
+void launch_build_lists(const ListArgs &a, cudaStream_t s);
+
+// ---- interact.cu ----
+struct DensArgs {
+  int n_active;
+  const int *active;     // active target leaves
+  const Leaf *leaves;
+  const int *list_off;   // [n_leaves + 1]
+  const Task *tasks;
+  const float4 *pm;
+  const float *hf;
+  const unsigned char *done;  // per particle converged flag
+  float4 *sums;          // sum w, sum q w', sum m w, sum m (3w + q w')
+  int *cnt;
+  DevCounters *ctr;
+  int kahan;
+};
+void launch_density(const DensArgs &a, cudaStream_t s);
+
+struct GhostArgs {
+  int n;
+  double n_ngb, tol, gamma;
+  int max_iter;
+  const Leaf *leaves;
+  const int *leaf_of;     // per particle leaf index
+  const Node *nodes;
+  const BoxDev *boxes;
+  int n_boxes;
+  float cap_factor;
+  double *h;
+  double *hlo, *hhi;
+  float *hf;
+  const float4 *sums;
+  const int *cnt;
+  const float4 *vu;       // u in .w (predicted u during a step)
+  unsigned char *done;
+  int *niter;
+  int *nngb;
+  float *rho, *omega, *P;
+  float4 *force_i;        // (h, 1/h, A (8/pi) h^-4, m) for the force stage
+  DevCounters *ctr;
+};
+void launch_ghost(const GhostArgs &a, cudaStream_t s);
+void launch_active_leaves(const Leaf *leaves, int n_leaves, const unsigned char *done,
+                          int *active, DevCounters *ctr, cudaStream_t s);
+
+struct ForceArgs {
+  int n_leaves;
+  const Leaf *leaves;
+  const int *list_off;
+  const Task *tasks;
+  const float4 *pm;
+  const float4 *fi;       // (h, 1/h, A', m)
+  const float4 *vu;       // predicted v, u
+  float4 *acc;            // out: a, du/dt
+  int *nforce;
+  DevCounters *ctr;
+  int kahan;
+};
+void launch_force(const ForceArgs &a, cudaStream_t s);
+
+// ---- integrate.cu ----
+struct StoreArrays {
+  double *x0, *x1, *x2, *h, *hlo, *hhi;
+  float4 *vu, *vu_pred, *acc;
+  float *m;
+  int *orig;
+};
+// wx: wrapped caller-order positions, SoA (x0 = wx, x1 = wx + n, x2 = wx + 2n)
+void launch_load_caller(const StoreArrays &dst, const int *order, int n, const double *wx,
+                        const float *v, const float *m, const float *u, const double *h,
+                        cudaStream_t s);
+void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *order, int n,
+                    cudaStream_t s);
+void launch_wrap_cell_keys_from_caller(const double *x, const BoxDev *boxes, int n_boxes, int n,
+                                       double *x0, double *x1, double *x2, cudaStream_t s);
+void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
+                       DevCounters *ctr, cudaStream_t s);
+void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s);
+void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
+void launch_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of, cudaStream_t s);
+void launch_get(int field, void *out, const int *orig, int n, const StoreArrays &st,
+                const float *rho, const float *omega, const float *P, const int *nngb,
+                const int *niter, const int *nforce, cudaStream_t s);
+
+}  // namespace sph

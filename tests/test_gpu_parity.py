@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded inputs, at sizes the oracle finishes in seconds
+(several leaves and top cells, ragged particle counts)."""
+import numpy as np
+import pytest
+
+from paper_1606_02738_gb300 import inputs
+from paper_1606_02738_gb300 import sph
+from _parity import (compare_density, compare_force, force_counts_close, run_gpu,
+                     run_oracle)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sph.lib()
+
+
+@pytest.mark.parametrize("mode", [sph.SPH_MODE_PLAIN])
+@pytest.mark.parametrize("n_split", [64, 17])
+def test_uniform_ragged_density_force(mode, n_split):
+    p = inputs.uniform(6007, seed=101, sigma_v=0.3)
+    g = run_gpu(p, n_split=n_split, mode=mode)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
+    force_counts_close(g, s)
+    st = g["stats"]
+    assert st["density_interactions"] == pytest.approx(s.n_dens.sum(), rel=1e-5)
+    assert st["force_interactions"] == pytest.approx(s.n_force.sum(), rel=1e-5)
+
+
+def test_config1_uniform_32k():
+    p = inputs.config(1)
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)  # v = 0: du/dt must vanish exactly
+    assert np.all(g["dudt"] == 0.0)
+
+
+def test_config1_uniform_32k_moving():
+    p = inputs.uniform(32768, seed=inputs.SEED_BASE + 1, sigma_v=0.1)
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
+
+
+@pytest.mark.parametrize("precision", [sph.SPH_PREC_FP32, sph.SPH_PREC_KAHAN])
+def test_clustered_h_spread(precision):
+    p = inputs.clustered(30011, n_spheres=8, seed=7, sigma_v=0.2)
+    g = run_gpu(p, precision=precision)
+    s = run_oracle(p)
+    assert s.h.max() / s.h.min() > 20
+    compare_density(g, s)
+    compare_force(g, s)
+    force_counts_close(g, s)
+
+
+def test_batched_boxes():
+    p = inputs.batched(n_boxes=6, n_min=300, n_max=6000, seed=99)
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
+
+
+def test_lognormal_small():
+    p = inputs.lognormal(n=40000, grid=32, seed=5)
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
+
+
+def test_lattice_on_cell_faces_and_box_edge():
+    """Lattice through the origin (particles on the box faces and on every
+    top-cell face): uniform rho and h, forces zero up to FP32 round-off."""
+    n = 20
+    a = 1.0 / n
+    g1 = np.arange(n) * a
+    x = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    p = inputs._single("lattice_faces", x, np.zeros_like(x), 1.0 / x.shape[0], 1.0, 2.4 * a,
+                       [1.0, 1.0, 1.0])
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    assert np.ptp(g["h"]) / g["h"][0] < 1e-6
+    # size of one pair term m_j A_i |dW/dr| near its maximum (|w'| <= 2)
+    A = (s.gamma - 1) * s.u[0] / (s.omega[0] * s.rho[0])
+    scale = s.m[0] * A * (8 / np.pi) * 2 / s.h[0] ** 4
+    assert np.abs(g["a"]).max() < 1e-4 * scale
+
+
+def test_sod_kdk_steps():
+    p = inputs.sod(nx_left=96, n_yz_left=24, nx_right=48, n_yz_right=12)
+    dt = 2e-3
+    g = run_gpu(p, steps=3, dt=dt)
+    s = run_oracle(p, steps=3, dt=dt)
+    compare_density(g, s, tol_rho=2e-5, tol_h=2e-5, counts=False)
+    compare_force(g, s, tol_a=3e-4, tol_du=3e-4)
+    np.testing.assert_allclose(g["x"], s.x, rtol=0, atol=1e-9)
+    mom = (s.m[:, None] * g["v"].astype(np.float64)).sum(axis=0)
+    assert np.abs(mom).max() < 1e-6 * (s.m[:, None] * np.abs(g["v"])).sum()
+
+
+def test_deterministic_repeat():
+    p = inputs.clustered(12000, n_spheres=4, seed=3, sigma_v=0.1)
+    g1 = run_gpu(p)
+    g2 = run_gpu(p)
+    for k in ("h", "rho", "a", "dudt", "nngb"):
+        np.testing.assert_array_equal(g1[k], g2[k])
+
+
+def test_error_codes():
+    from paper_1606_02738_gb300.sph import Context, SphError
+    p = inputs.uniform(20, seed=1)   # too few particles: h would exceed L/3
+    c = Context().load(p)
+    with pytest.raises(SphError) as e:
+        c.density()
+    assert e.value.code == sph.SPH_EBOXTOOSMALL
+    c.close()
+    q = inputs.uniform(500, seed=2)
+    q.m[3] = -1.0
+    with pytest.raises(SphError) as e:
+        Context().load(q)
+    assert e.value.code == sph.SPH_EINVAL
+    q = inputs.uniform(500, seed=2)
+    c = Context().load(q)
+    with pytest.raises(SphError) as e:
+        c.force()
+    assert e.value.code == sph.SPH_ESTATE
+    with pytest.raises(SphError) as e:
+        c.get("rho")
+    assert e.value.code == sph.SPH_ESTATE
+    c.close()
+
+
+def test_empty_box_among_others():
+    a = inputs.uniform(3000, seed=4)
+    b = inputs.uniform(2500, seed=5)
+    p = inputs.ParticleSet(
+        name="with_empty", x=np.concatenate([a.x, b.x]), v=np.concatenate([a.v, b.v]),
+        m=np.concatenate([a.m, b.m]), u=np.concatenate([a.u, b.u]),
+        h=np.concatenate([a.h, b.h]), box=np.ones((3, 3)),
+        box_offsets=np.array([0, 3000, 3000, 5500], dtype=np.int64))
+    g = run_gpu(p)
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
