@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the SPH hot path: neighbour interactions per second
+(density + force) on one GB300, and the fraction of the FP32 roofline.
+
+One step = one full kick-drift-kick step of the 3D Sod shock tube (972,000
+particles, periodic [0,2]x[0,0.25]^2): drift, cell grid (A1), octree split
+(A2), density with the smoothing-length iteration (A4, A5), force (A6) and
+the kicks (A7). The metric counts density interactions of the converged pass
+(ordered pairs j != i, r_ij < h_i) plus force interactions (r_ij <
+max(h_i, h_j)) and divides by the device time of the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded
+sample of the same workload). With torchrun (N > 1) every rank runs an
+independent replica (the workload does not shard across GPUs; "replicas
+only") and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH neighbour interactions/sec (density+force) on 1 GB300; % FP32 roofline"
+UNIT = "interactions/s"
+FLOPS_DENSITY = 29   # per density interaction (FFMA = 2)
+FLOPS_FORCE = 44     # per force interaction
+SOD_DT = 7e-4        # 0.1 * min(h / c) of the initial state, rounded down
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["plain", "batched"], default="plain")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sod", choices=["sod", "uniform", "clustered",
+                                                          "batched", "lognormal"])
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1606_02738_gb300 import inputs
+    if name == "sod":
+        return inputs.config(2), SOD_DT, "sod3d_972k"
+    if name == "uniform":
+        return inputs.config(1), 1e-3, "uniform_32k"
+    if name == "clustered":
+        return inputs.config(3), 2e-4, "plummer_clustered_4M"
+    if name == "batched":
+        return inputs.config(4), 2e-4, "batched_256_boxes"
+    return inputs.config(5), 2e-4, "lognormal_64M"
+
+
+# ----------------------------------------------------------- distributed
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def reduce(self, value: float, op: str) -> float:
+        if not self.pg:
+            return value
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=getattr(self.pg.ReduceOp, op))
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- roofline
+
+def fp32_peak_tflops(sm_count: int) -> tuple[float, str]:
+    mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mhz = float(mp.get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+    return peak, (f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop/FFMA x {mhz:.0f} MHz "
+                  f"(MEASURED_PEAKS.json sm_max_mhz)")
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu capture, only while the
+    kernel source it was taken on is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1606_02738_gb300", "csrc", "interact.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha") != h:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(p, budget_s: float = 30.0) -> dict:
+    """The FP64 oracle, as it stands, on one density + force evaluation of
+    the workload (all particles), on this host's cores."""
+    import oracle
+    oracle.build()
+    s = oracle.State.from_particles(p)
+    t0 = time.perf_counter()
+    oracle.compute_density(s)
+    oracle.compute_force(s)
+    dt = time.perf_counter() - t0
+    inter = int(s.n_dens.sum() + s.n_force.sum())
+    return {"value": inter / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one h-iterated density + force evaluation of all {p.n} particles of "
+                      f"the initial state ({inter} interactions, {dt:.2f} s)",
+            "seconds": dt}
+
+
+def run_reference(args, d: Dist):
+    """--impl reference: the oracle on the host cores, each step a bounded
+    sample (density + force of a seeded particle subset, full neighbour
+    context) of the same workload."""
+    if d.rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    p, dt, wname = workload(args.workload)
+    s = oracle.State.from_particles(p)
+    oracle.compute_density(s)          # untimed set-up: every h, rho, Omega
+    total = args.steps + args.warmup
+    frac = min(1.0, 8.0 / max(1, total))
+    n_sub = max(1000, int(p.n * frac))
+    rng = np.random.default_rng(7)
+    inter = 0
+    t_timed = 0.0
+    for k in range(total):
+        sub = np.sort(rng.choice(p.n, size=min(n_sub, p.n), replace=False))
+        t0 = time.perf_counter()
+        dd = oracle.density(s.x, s.m, s.box[0], s.h, s.n_ngb, subset=sub)
+        ff = oracle.force(s.x, s.v, s.m, s.u, s.h, s.rho, s.omega, s.box[0], s.gamma, subset=sub)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            t_timed += el
+            inter += int(dd["count"][sub].sum() + ff["count"][sub].sum())
+    value = inter / t_timed
+    sample = (f"each step: h-iterated density + force of a seeded subset of {n_sub} of the "
+              f"{p.n} particles (k-d tree over all), {args.steps} timed steps")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * t_timed / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wname, "n_particles": p.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- ours
+
+def run_ours(args, d: Dist):
+    import torch
+    from paper_1606_02738_gb300 import sph
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(d.local)
+    dev = torch.device("cuda", d.local)
+    p, dt, wname = workload(args.workload)
+    mode = sph.SPH_MODE_BATCHED if args.mode == "batched" else sph.SPH_MODE_PLAIN
+    stream = torch.cuda.current_stream(dev)
+    ctx = sph.Context(mode=mode, profile=True, device=dev)
+    ctx.load(p)
+    ctx.density()
+    ctx.force()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    for _ in range(args.warmup):
+        ctx.step(dt, 1)
+    torch.cuda.synchronize(dev)
+    s0 = ctx.stats()
+    d.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(d.local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))             # evict L2 between timed steps (not timed)
+        ev[k][0].record(stream)
+        ctx.step(dt, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    d.barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    s1 = ctx.stats()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    inter_d = s1["total_density_interactions"] - s0["total_density_interactions"]
+    inter_f = s1["total_force_interactions"] - s0["total_force_interactions"]
+    inter = inter_d + inter_f
+    ms_max = d.reduce(ms, "MAX")
+    inter_all = d.reduce(float(inter), "SUM")
+    value = inter_all / (ms_max / 1000.0)
+
+    # roofline of the interaction kernels (CUDA events around each launch,
+    # recorded by the library on this stream)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, peak_src = fp32_peak_tflops(sm_count)
+    kern = {}
+    for name, flops, t_key, n_key, ikey in (
+            ("density", FLOPS_DENSITY, "t_density_ms", "density_launches", inter_d),
+            ("force", FLOPS_FORCE, "t_force_ms", "force_launches", inter_f)):
+        t = s1[t_key] - s0[t_key]
+        n = max(1, s1[n_key] - s0[n_key])
+        achieved = flops * ikey / (t / 1000.0) / 1e12 if t > 0 else 0.0
+        kern[name] = {"achieved": achieved, "launches": n, "ms_per_launch": t / n,
+                      "share_of_step": t / ms if ms > 0 else 0.0,
+                      "flops_per_launch": flops * ikey / n}
+    dom = max(kern, key=lambda k: kern[k]["share_of_step"])
+    roof = {"bound": "alu", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
+            "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom),
+            "kernel": dom, "peak_source": peak_src,
+            "flops_per_interaction": {"density": FLOPS_DENSITY, "force": FLOPS_FORCE},
+            "kernels": kern}
+    stages = {k: (s1[k] - s0[k]) / args.steps for k in
+              ("t_grid_ms", "t_lists_ms", "t_density_ms", "t_ghost_ms", "t_force_ms",
+               "t_integrate_ms")}
+
+    # end to end through the C ABI with host buffers: H2D of the inputs from
+    # pinned memory, init + density + force + one KDK step, D2H of x, v, u, h
+    host = {k: torch.as_tensor(getattr(p, k)).pin_memory() for k in ("x", "v", "m", "u", "h")}
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    outs = {"x": torch.empty((p.n, 3), dtype=torch.float64).pin_memory(),
+            "v": torch.empty((p.n, 3), dtype=torch.float32).pin_memory(),
+            "u": torch.empty(p.n, dtype=torch.float32).pin_memory(),
+            "h": torch.empty(p.n, dtype=torch.float64).pin_memory()}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in outs.values())
+    e2e_ms, e2e_inter = 0.0, 0
+    for k in range(args.e2e_steps + 1):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        sa = ctx.stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for key in host:
+            dbuf[key].copy_(host[key], non_blocking=True)
+        sph.sph_init(ctx.ctx, p.box_offsets, p.box, **dbuf)
+        ctx.density()
+        ctx.force()
+        ctx.step(dt, 1)
+        for key, out in outs.items():
+            out.copy_(ctx.get(key), non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        sb = ctx.stats()
+        if k == 0:
+            continue  # first pass warms the allocations
+        e2e_ms += a.elapsed_time(b)
+        e2e_inter += (sb["total_density_interactions"] - sa["total_density_interactions"] +
+                      sb["total_force_interactions"] - sa["total_force_interactions"])
+    e2e_ms_max = d.reduce(e2e_ms, "MAX")
+    e2e_val = d.reduce(float(e2e_inter), "SUM") / (e2e_ms_max / 1000.0)
+
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p)
+
+    if d.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wname, "n_particles": p.n, "dt": dt,
+                       "step": "one kick-drift-kick step: regrid, density (h iteration), "
+                               "force, kicks",
+                       "mode": args.mode, "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": "replicas" if d.world > 1 else "single GPU",
+                       "interactions_per_step": inter / args.steps,
+                       "density_passes_last_step": s1["density_passes"],
+                       "leaves": s1["n_leaves"]},
+            "roofline": roof,
+            "stage_ms_per_step": stages,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "step": "H2D inputs, sph_init, sph_density, sph_force, sph_step(dt, 1), "
+                            "D2H x v u h"},
+            "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    d = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, d)
+        else:
+            run_ours(args, d)
+    finally:
+        d.close()
+
+
+if __name__ == "__main__":
+    main()

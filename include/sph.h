@@ -85,7 +85,8 @@ typedef struct {
   int n_split;     /* split octree cells holding more particles than this (8..256) */
   int precision;   /* SPH_PREC_* */
   int mode;        /* SPH_MODE_* */
-  int reserved[4]; /* zero */
+  int profile;     /* 1: time each stage with CUDA events on the context stream */
+  int reserved[3]; /* zero */
 } sph_params;
 
 typedef struct {
@@ -104,6 +105,21 @@ typedef struct {
   int32_t max_iter_used;      /* most passes any particle needed */
   int32_t reserved;
   double h_min, h_max;        /* extremes of the converged h */
+  /* Cumulative since sph_create (never reset): */
+  int64_t total_density_interactions; /* converged-pass density interactions */
+  int64_t total_force_interactions;
+  int64_t kernel_launches;    /* CUDA kernels this context enqueued */
+  int64_t density_launches;   /* launches of the density interaction kernel */
+  int64_t force_launches;     /* launches of the force interaction kernel */
+  /* Stage times in ms (CUDA events on the context stream; profile = 1 only).
+   * Each brackets the stage's launches; stages that read device counters
+   * back include the host round trip. */
+  double t_grid_ms;           /* cell keys, counting sort, octree split, gather */
+  double t_lists_ms;          /* leaf-pair task lists */
+  double t_density_ms;        /* density interaction kernel only */
+  double t_ghost_ms;          /* h update / finalisation kernel */
+  double t_force_ms;          /* force interaction kernel only */
+  double t_integrate_ms;      /* kick / drift kernels */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,

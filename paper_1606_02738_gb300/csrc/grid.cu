@@ -103,16 +103,16 @@ void exclusive_scan_int(const int *in, int *out, int n, void *tmp, size_t tmp_by
                         cudaStream_t s) {
   if (n <= 0) return;
   if (n <= kScanTile) {
-    k_scan_apply<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    k_scan_apply<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr); note_launch();
     return;
   }
   const int nb = (n + kScanTile - 1) / kScanTile;
   int *bsum = reinterpret_cast<int *>(tmp);
   int *boff = bsum + nb + 1;
   void *rest = boff + nb + 1;
-  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, bsum);
+  k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, bsum); note_launch();
   exclusive_scan_int(bsum, boff, nb, rest, tmp_bytes, s);
-  k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, boff);
+  k_scan_apply<<<nb, kScanThreads, 0, s>>>(in, out, n, boff); note_launch();
 }
 
 // ------------------------------------------------------------- helpers
@@ -184,7 +184,7 @@ __global__ void k_cell_keys(GridArgs g) {
 }
 
 void launch_cell_keys(const GridArgs &g, cudaStream_t s) {
-  k_cell_keys<<<(g.n + 255) / 256, 256, 0, s>>>(g);
+  k_cell_keys<<<(g.n + 255) / 256, 256, 0, s>>>(g); note_launch();
 }
 
 // Scatter into cell ranges. The slot order inside a cell is settled later
@@ -200,7 +200,7 @@ __global__ void k_cell_scatter(GridArgs g) {
 }
 
 void launch_cell_scatter(const GridArgs &g, cudaStream_t s) {
-  k_cell_scatter<<<(g.n + 255) / 256, 256, 0, s>>>(g);
+  k_cell_scatter<<<(g.n + 255) / 256, 256, 0, s>>>(g); note_launch();
 }
 
 // ------------------------------------------------------------------ A2
@@ -231,7 +231,7 @@ __global__ void k_init_top_nodes(Node *nodes, GridArgs g) {
 }
 
 void launch_init_top_nodes(Node *nodes, const GridArgs &g, cudaStream_t s) {
-  k_init_top_nodes<<<(g.n_cells + 255) / 256, 256, 0, s>>>(nodes, g);
+  k_init_top_nodes<<<(g.n_cells + 255) / 256, 256, 0, s>>>(nodes, g); note_launch();
 }
 
 __global__ void k_frontier_top(const Node *nodes, int n_cells, int n_split, int *frontier,
@@ -243,7 +243,7 @@ __global__ void k_frontier_top(const Node *nodes, int n_cells, int n_split, int 
 
 void launch_frontier_top(const Node *nodes, int n_cells, int n_split, int *frontier,
                          DevCounters *ctr, cudaStream_t s) {
-  k_frontier_top<<<(n_cells + 255) / 256, 256, 0, s>>>(nodes, n_cells, n_split, frontier, ctr);
+  k_frontier_top<<<(n_cells + 255) / 256, 256, 0, s>>>(nodes, n_cells, n_split, frontier, ctr); note_launch();
 }
 
 // One block per node to split: count its particles per octant, lay the 8
@@ -313,7 +313,7 @@ void launch_split_level(Node *nodes, const int *frontier, int n_frontier, int ch
                         const GridArgs &g, cudaStream_t s) {
   if (n_frontier <= 0) return;
   k_split<<<n_frontier, 256, 0, s>>>(nodes, frontier, n_frontier, child_base, level, n_split,
-                                     next_frontier, ctr, g);
+                                     next_frontier, ctr, g); note_launch();
 }
 
 __global__ void k_mark_leaves(const Node *nodes, int n_nodes, int *flag) {
@@ -324,7 +324,7 @@ __global__ void k_mark_leaves(const Node *nodes, int n_nodes, int *flag) {
 }
 
 void launch_mark_leaves(const Node *nodes, int n_nodes, int *flag, cudaStream_t s) {
-  k_mark_leaves<<<(n_nodes + 255) / 256, 256, 0, s>>>(nodes, n_nodes, flag);
+  k_mark_leaves<<<(n_nodes + 255) / 256, 256, 0, s>>>(nodes, n_nodes, flag); note_launch();
 }
 
 __global__ void k_fill_leaves(Node *nodes, int n_nodes, const int *excl, Leaf *leaves,
@@ -351,7 +351,7 @@ __global__ void k_fill_leaves(Node *nodes, int n_nodes, const int *excl, Leaf *l
 void launch_fill_leaves(Node *nodes, int n_nodes, const int *leaf_idx_excl, Leaf *leaves,
                         const BoxDev *boxes, int n_boxes, cudaStream_t s) {
   k_fill_leaves<<<(n_nodes + 255) / 256, 256, 0, s>>>(nodes, n_nodes, leaf_idx_excl, leaves,
-                                                      boxes, n_boxes);
+                                                      boxes, n_boxes); note_launch();
 }
 
 // Order each leaf's particles by original index (insertion sort; leaves are
@@ -376,7 +376,7 @@ __global__ void k_sort_leaves(const Leaf *leaves, int n_leaves, int *order, cons
 
 void launch_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig,
                         cudaStream_t s) {
-  k_sort_leaves<<<(n_leaves + 127) / 128, 128, 0, s>>>(leaves, n_leaves, order, orig);
+  k_sort_leaves<<<(n_leaves + 127) / 128, 128, 0, s>>>(leaves, n_leaves, order, orig); note_launch();
 }
 
 // --------------------------------------------------- leaf geometry / hmax
@@ -458,13 +458,13 @@ __global__ void k_leaf_hmax(GeomArgs a) {
 
 void launch_leaf_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s) {
   if (a.n_leaves <= 0) return;
-  k_leaf_geometry<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a);
+  k_leaf_geometry<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
 void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s) {
-  k_reset_hmax<<<(n_nodes + 255) / 256, 256, 0, s>>>(a.nodes, n_nodes);
+  k_reset_hmax<<<(n_nodes + 255) / 256, 256, 0, s>>>(a.nodes, n_nodes); note_launch();
   if (a.n_leaves <= 0) return;
-  k_leaf_hmax<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a);
+  k_leaf_hmax<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
 // ------------------------------------------------------------ task lists
@@ -537,7 +537,7 @@ __global__ void k_lists(ListArgs a) {
 
 void launch_build_lists(const ListArgs &a, cudaStream_t s) {
   if (a.n_targets <= 0) return;
-  k_lists<<<(a.n_targets + 127) / 128, 128, 0, s>>>(a);
+  k_lists<<<(a.n_targets + 127) / 128, 128, 0, s>>>(a); note_launch();
 }
 
 }  // namespace sph

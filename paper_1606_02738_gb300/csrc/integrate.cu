@@ -45,7 +45,7 @@ __global__ void k_wrap_from_caller(const double *x, const BoxDev *boxes, int nb,
 
 void launch_wrap_cell_keys_from_caller(const double *x, const BoxDev *boxes, int n_boxes, int n,
                                        double *x0, double *x1, double *x2, cudaStream_t s) {
-  k_wrap_from_caller<<<(n + 255) / 256, 256, 0, s>>>(x, boxes, n_boxes, n, x0, x1, x2);
+  k_wrap_from_caller<<<(n + 255) / 256, 256, 0, s>>>(x, boxes, n_boxes, n, x0, x1, x2); note_launch();
 }
 
 // Sorted store <- caller arrays; `order[s]` is the caller index of slot s.
@@ -81,7 +81,7 @@ void launch_load_caller(const StoreArrays &dst, const int *order, int n, const d
                         const float *v, const float *m, const float *u, const double *h,
                         cudaStream_t s) {
   LoadArgs a{dst, order, n, wx, wx + n, wx + 2 * (size_t)n, v, m, u, h};
-  k_load<<<(n + 255) / 256, 256, 0, s>>>(a);
+  k_load<<<(n + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
 __global__ void k_permute(StoreArrays d, StoreArrays src, const int *order, int n) {
@@ -103,7 +103,7 @@ __global__ void k_permute(StoreArrays d, StoreArrays src, const int *order, int 
 
 void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *order, int n,
                     cudaStream_t s) {
-  k_permute<<<(n + 255) / 256, 256, 0, s>>>(dst, src, order, n);
+  k_permute<<<(n + 255) / 256, 256, 0, s>>>(dst, src, order, n); note_launch();
 }
 
 // First half kick, drift, prediction.
@@ -131,7 +131,7 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
                        DevCounters *ctr, cudaStream_t s) {
-  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, ctr);
+  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, ctr); note_launch();
 }
 
 // Closing half kick with the new accelerations.
@@ -151,7 +151,7 @@ __global__ void k_kick(StoreArrays st, int n, double dt, DevCounters *ctr) {
 }
 
 void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s) {
-  k_kick<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, ctr);
+  k_kick<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, ctr); note_launch();
 }
 
 __global__ void k_h_to_float(const double *h, float *hf, int n) {
@@ -160,7 +160,7 @@ __global__ void k_h_to_float(const double *h, float *hf, int n) {
 }
 
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
-  k_h_to_float<<<(n + 255) / 256, 256, 0, s>>>(h, hf, n);
+  k_h_to_float<<<(n + 255) / 256, 256, 0, s>>>(h, hf, n); note_launch();
 }
 
 __global__ void k_h_extremes(const double *h, int n, const BoxDev *boxes, int nb,
@@ -175,7 +175,7 @@ __global__ void k_h_extremes(const double *h, int n, const BoxDev *boxes, int nb
 
 void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
                        unsigned long long *dmax, unsigned long long *dminmax, cudaStream_t s) {
-  k_h_extremes<<<(n + 255) / 256, 256, 0, s>>>(h, n, boxes, n_boxes, dmax, dminmax);
+  k_h_extremes<<<(n + 255) / 256, 256, 0, s>>>(h, n, boxes, n_boxes, dmax, dminmax); note_launch();
 }
 
 __global__ void k_validate(const double *x, const float *v, const float *m, const float *u,
@@ -191,7 +191,7 @@ __global__ void k_validate(const double *x, const float *v, const float *m, cons
 
 void launch_validate(const double *x, const float *v, const float *m, const float *u,
                      const double *h, int n, int *status, cudaStream_t s) {
-  k_validate<<<(n + 255) / 256, 256, 0, s>>>(x, v, m, u, h, n, status);
+  k_validate<<<(n + 255) / 256, 256, 0, s>>>(x, v, m, u, h, n, status); note_launch();
 }
 
 __global__ void k_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi,
@@ -206,7 +206,7 @@ __global__ void k_reset_iteration(unsigned char *done, int *niter, double *hlo, 
 
 void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi, int n,
                             cudaStream_t s) {
-  k_reset_iteration<<<(n + 255) / 256, 256, 0, s>>>(done, niter, hlo, hhi, n);
+  k_reset_iteration<<<(n + 255) / 256, 256, 0, s>>>(done, niter, hlo, hhi, n); note_launch();
 }
 
 __global__ void k_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of) {
@@ -217,7 +217,7 @@ __global__ void k_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of) {
 }
 
 void launch_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of, cudaStream_t s) {
-  k_leaf_of<<<(n_leaves + 255) / 256, 256, 0, s>>>(leaves, n_leaves, leaf_of);
+  k_leaf_of<<<(n_leaves + 255) / 256, 256, 0, s>>>(leaves, n_leaves, leaf_of); note_launch();
 }
 
 struct GetArgs {
@@ -273,7 +273,7 @@ void launch_get(int field, void *out, const int *orig, int n, const StoreArrays 
                 const float *rho, const float *omega, const float *P, const int *nngb,
                 const int *niter, const int *nforce, cudaStream_t s) {
   GetArgs a{field, out, orig, n, st, rho, omega, P, nngb, niter, nforce};
-  k_get<<<(n + 255) / 256, 256, 0, s>>>(a);
+  k_get<<<(n + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
 }  // namespace sph

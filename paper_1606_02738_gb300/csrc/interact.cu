@@ -130,6 +130,7 @@ void launch_density(const DensArgs &a, cudaStream_t s) {
     k_density<true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
   else
     k_density<false><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
+  note_launch();
 }
 
 // ------------------------------------------------------------------ ghost
@@ -214,7 +215,7 @@ __global__ void k_ghost(GhostArgs a) {
 }
 
 void launch_ghost(const GhostArgs &a, cudaStream_t s) {
-  k_ghost<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  k_ghost<<<(a.n + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
 __global__ void k_active_leaves(const Leaf *leaves, int n_leaves, const unsigned char *done,
@@ -229,7 +230,7 @@ __global__ void k_active_leaves(const Leaf *leaves, int n_leaves, const unsigned
 
 void launch_active_leaves(const Leaf *leaves, int n_leaves, const unsigned char *done,
                           int *active, DevCounters *ctr, cudaStream_t s) {
-  k_active_leaves<<<(n_leaves + 255) / 256, 256, 0, s>>>(leaves, n_leaves, done, active, ctr);
+  k_active_leaves<<<(n_leaves + 255) / 256, 256, 0, s>>>(leaves, n_leaves, done, active, ctr); note_launch();
 }
 
 // ------------------------------------------------------------------ force
@@ -330,6 +331,7 @@ void launch_force(const ForceArgs &a, cudaStream_t s) {
     k_force<true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
   else
     k_force<false><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);
+  note_launch();
 }
 
 }  // namespace sph

@@ -45,6 +45,9 @@ struct sph_ctx {
   char *ws = nullptr;
   size_t ws_bytes = 0, ws_used = 0;
   std::vector<void *> owned;
+  int64_t alloc_n = -1;  // store currently laid out for (alloc_n, alloc_nb, alloc_ws)
+  int alloc_nb = -1;
+  char *alloc_ws = nullptr;
 
   int n = 0, nb = 0;
   std::vector<BoxDev> boxes_h;
@@ -72,8 +75,51 @@ struct sph_ctx {
 
   bool loaded = false, grid_valid = false, density_valid = false, force_valid = false;
   int last_passes = 0, last_rebuilds = 0;
-  unsigned long long dens_cand_total = 0;
+  // cumulative counters and stage timers
+  long long launches = 0, dens_launches = 0, force_launches = 0;
+  unsigned long long total_dens_inter = 0, total_force_inter = 0;
+  bool force_pending = false;  // force counters on the device not yet added to the totals
+  cudaEvent_t ev[6][2] = {};
+  bool ev_pending[6] = {};
+  double t_ms[6] = {};
 };
+
+namespace sph {
+thread_local long long *g_launch_count = nullptr;
+}
+
+namespace {
+
+enum Stage { kGrid = 0, kLists, kDens, kGhost, kForce, kInteg };
+
+// Points the launch counter at this context for the duration of an API call.
+struct LaunchScope {
+  long long *prev;
+  explicit LaunchScope(sph_ctx *c) : prev(g_launch_count) { g_launch_count = &c->launches; }
+  ~LaunchScope() { g_launch_count = prev; }
+};
+
+void tic(sph_ctx *c, Stage s) {
+  if (c->p.profile) cudaEventRecord(c->ev[s][0], c->stream);
+}
+void toc(sph_ctx *c, Stage s) {
+  if (!c->p.profile) return;
+  cudaEventRecord(c->ev[s][1], c->stream);
+  c->ev_pending[s] = true;
+}
+// Add the elapsed time of every bracket whose closing event was recorded.
+void collect_timers(sph_ctx *c) {
+  if (!c->p.profile) return;
+  for (int s = 0; s < 6; ++s) {
+    if (!c->ev_pending[s]) continue;
+    if (cudaEventSynchronize(c->ev[s][1]) != cudaSuccess) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[s][0], c->ev[s][1]) == cudaSuccess) c->t_ms[s] += ms;
+    c->ev_pending[s] = false;
+  }
+}
+
+}  // namespace
 
 namespace {
 
@@ -174,6 +220,8 @@ FixedLayout fixed_layout(int64_t n, int nb) {
 }
 
 int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
+  if (c->alloc_n == n && c->alloc_nb == nb && c->alloc_ws == c->ws) return SPH_OK;  // reuse
+  c->alloc_n = -1;
   FixedLayout L = fixed_layout(n, nb);
   for (void *p : c->owned) cudaFree(p);
   c->owned.clear();
@@ -236,6 +284,9 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   take(c->wx);
   take(c->hext);
   take(c->boxes_d);
+  c->alloc_n = n;
+  c->alloc_nb = nb;
+  c->alloc_ws = c->ws;
   return SPH_OK;
 }
 
@@ -248,6 +299,11 @@ int read_counters(sph_ctx *c) {
   CUDA_TRY(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
                            c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->force_pending) {
+    c->total_force_inter += c->ctr_h->force_inter;
+    c->force_pending = false;
+  }
+  collect_timers(c);
   return SPH_OK;
 }
 
@@ -281,7 +337,7 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
     const double hm = hmax_box[b] * (1.0 + 1e-6);
     const double lmin = std::min(B.L[0], std::min(B.L[1], B.L[2]));
     if (!(hm > 0.0)) return fail(c, SPH_EINVAL, "box %d has a non-positive smoothing length", b);
-    if (hm > lmin / 3.0)
+    if (hm > lmin / 3.0 * (1.0 + 1e-12))
       return fail(c, SPH_EBOXTOOSMALL, "box %d: h = %g exceeds L/3 = %g", b, hmax_box[b],
                   lmin / 3.0);
     const int64_t cap = std::max<int64_t>(27, 2 * (int64_t)B.count);
@@ -333,7 +389,7 @@ int h_extremes(sph_ctx *c, const double *h, std::vector<double> &hmax_box, doubl
 // A1 + A2: grid, recursive split, leaves, store gather, leaf geometry.
 // from_caller: positions come from the wrapped caller copy (c->wx) and the
 // store is loaded from the caller arrays passed in.
-int build_grid(sph_ctx *c, bool from_caller, const float *cv, const float *cm, const float *cu,
+int build_grid_inner(sph_ctx *c, bool from_caller, const float *cv, const float *cm, const float *cu,
                const double *ch) {
   std::vector<double> hmax_box;
   double hmin, hmax;
@@ -442,14 +498,22 @@ int build_grid(sph_ctx *c, bool from_caller, const float *cv, const float *cm, c
   return SPH_OK;
 }
 
+int build_grid(sph_ctx *c, bool from_caller, const float *cv, const float *cm, const float *cu,
+               const double *ch) {
+  tic(c, kGrid);
+  int rc = build_grid_inner(c, from_caller, cv, cm, cu, ch);
+  toc(c, kGrid);
+  return rc;
+}
+
 GeomArgs geom_args(sph_ctx *c) {
   return GeomArgs{c->n_leaves, as<Leaf>(c->leaves), as<Node>(c->nodes), c->boxes_d, c->nb,
                   c->st.x0, c->st.x1, c->st.x2, c->st.m, c->hf, c->pm};
 }
 
 // Count pass, scan, fill pass of a task list over `n_targets` target leaves.
-int build_lists(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf &off,
-                DevBuf &tasks, int64_t &n_tasks) {
+int build_lists_inner(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf &off,
+                      DevBuf &tasks, int64_t &n_tasks) {
   TRY(ensure(c, off, sizeof(int) * (size_t)(n_targets + 1)));
   ListArgs la{};
   la.n_leaves = c->n_leaves;
@@ -480,6 +544,14 @@ int build_lists(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf
   launch_build_lists(la, c->stream);
   n_tasks = total;
   return sync_check(c);
+}
+
+int build_lists(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf &off,
+                DevBuf &tasks, int64_t &n_tasks) {
+  tic(c, kLists);
+  int rc = build_lists_inner(c, force, active, n_targets, off, tasks, n_tasks);
+  toc(c, kLists);
+  return rc;
 }
 
 int check_status(sph_ctx *c, int st) {
@@ -527,7 +599,10 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
     da.cnt = c->cnt;
     da.ctr = c->ctr;
     da.kahan = c->p.precision == SPH_PREC_KAHAN;
+    tic(c, kDens);
     launch_density(da, c->stream);
+    toc(c, kDens);
+    ++c->dens_launches;
     CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, 2 * sizeof(int), c->stream));
     GhostArgs gh{};
     gh.n = n;
@@ -556,7 +631,9 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
     gh.P = c->P;
     gh.force_i = c->fi;
     gh.ctr = c->ctr;
+    tic(c, kGhost);
     launch_ghost(gh, c->stream);
+    toc(c, kGhost);
     TRY(sync_check(c));
     TRY(read_counters(c));
     const int st = c->ctr_h->status;
@@ -578,6 +655,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
       return fail(c, SPH_ENOTCONVERGED, "smoothing lengths did not converge in %d passes",
                   c->p.max_iter);
   }
+  c->total_dens_inter += c->ctr_h->dens_inter;
   c->density_valid = true;
   c->force_valid = false;
   return SPH_OK;
@@ -585,6 +663,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
 
 int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
+  if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
   TRY(build_lists(c, true, nullptr, c->n_leaves, c->force_off, c->force_tasks,
@@ -603,7 +682,11 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   fa.nforce = c->nforce;
   fa.ctr = c->ctr;
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
+  tic(c, kForce);
   launch_force(fa, c->stream);
+  toc(c, kForce);
+  ++c->force_launches;
+  c->force_pending = true;
   TRY(sync_check(c));
   c->force_valid = true;
   return SPH_OK;
@@ -649,6 +732,14 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
     return SPH_ECUDA;
   }
   std::memset(c->ctr_h, 0, sizeof(DevCounters));
+  if (c->p.profile) {
+    for (auto &pair : c->ev)
+      for (auto &e : pair)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          cudaGetLastError();
+          c->p.profile = 0;
+        }
+  }
   *out = c;
   return SPH_OK;
 }
@@ -671,6 +762,7 @@ int sph_set_workspace(sph_ctx *c, void *dev_ptr, size_t bytes) {
 int sph_init(sph_ctx *c, int n_boxes, const int64_t *box_offsets, const double *box_len,
              const double *x, const float *v, const float *m, const float *u, const double *h) {
   if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
   c->err.clear();
   if (n_boxes < 1 || !box_offsets || !box_len || !x || !v || !m || !u || !h)
     return fail(c, SPH_EINVAL, "null argument or n_boxes < 1");
@@ -703,6 +795,7 @@ int sph_init(sph_ctx *c, int n_boxes, const int64_t *box_offsets, const double *
   if (c->ctr_h->status & kErrInvalidInput)
     return fail(c, SPH_EINVAL, "inputs must be finite with m > 0, u >= 0 and h > 0");
   k_iota<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->ident, c->n);
+  note_launch();
   launch_wrap_cell_keys_from_caller(x, c->boxes_d, c->nb, c->n, c->wx, c->wx + n,
                                     c->wx + 2 * (size_t)n, c->stream);
   TRY(build_grid(c, true, v, m, u, h));
@@ -712,6 +805,7 @@ int sph_init(sph_ctx *c, int n_boxes, const int64_t *box_offsets, const double *
 
 int sph_density(sph_ctx *c) {
   if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
   c->err.clear();
   if (!c->loaded) return fail(c, SPH_ESTATE, "sph_density before sph_init");
   return density_impl(c, c->st.vu);
@@ -719,6 +813,7 @@ int sph_density(sph_ctx *c) {
 
 int sph_force(sph_ctx *c) {
   if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
   c->err.clear();
   if (!c->loaded) return fail(c, SPH_ESTATE, "sph_force before sph_init");
   return force_impl(c, c->st.vu);
@@ -726,6 +821,7 @@ int sph_force(sph_ctx *c) {
 
 int sph_step(sph_ctx *c, double dt, int n_steps) {
   if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
   c->err.clear();
   if (!c->loaded || !c->force_valid)
     return fail(c, SPH_ESTATE, "sph_step needs sph_density and sph_force on the current state");
@@ -733,14 +829,18 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
     return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
   for (int s = 0; s < n_steps; ++s) {
     CUDA_TRY(cudaMemsetAsync(&c->ctr->status, 0, sizeof(int), c->stream));
+    tic(c, kInteg);
     launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+    toc(c, kInteg);
     c->grid_valid = false;
     c->density_valid = false;
     c->force_valid = false;
     TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
     TRY(density_impl(c, c->st.vu_pred));
     TRY(force_impl(c, c->st.vu_pred));
+    tic(c, kInteg);
     launch_kick(c->st, c->n, dt, c->ctr, c->stream);
+    toc(c, kInteg);
     TRY(read_counters(c));
     TRY(check_status(c, c->ctr_h->status));
   }
@@ -749,6 +849,7 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
 
 int sph_get(sph_ctx *c, int field, void *dev_out) {
   if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
   c->err.clear();
   if (!dev_out || field < 0 || field >= SPH_NFIELDS)
     return fail(c, SPH_EINVAL, "unknown field %d or null output", field);
@@ -767,6 +868,7 @@ int sph_get(sph_ctx *c, int field, void *dev_out) {
 
 int sph_stats(sph_ctx *c, sph_stats_t *out) {
   if (!c || !out) return SPH_EINVAL;
+  LaunchScope ls(c);
   std::memset(out, 0, sizeof *out);
   out->n_particles = c->n;
   out->n_boxes = c->nb;
@@ -783,6 +885,17 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->density_passes = c->last_passes;
   out->rebuilds = c->last_rebuilds;
   out->max_iter_used = c->ctr_h->max_iter_used;
+  out->total_density_interactions = (int64_t)c->total_dens_inter;
+  out->total_force_interactions = (int64_t)c->total_force_inter;
+  out->density_launches = c->dens_launches;
+  out->force_launches = c->force_launches;
+  out->t_grid_ms = c->t_ms[kGrid];
+  out->t_lists_ms = c->t_ms[kLists];
+  out->t_density_ms = c->t_ms[kDens];
+  out->t_ghost_ms = c->t_ms[kGhost];
+  out->t_force_ms = c->t_ms[kForce];
+  out->t_integrate_ms = c->t_ms[kInteg];
+  out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
   double hmin = 0, hmax = 0;
   TRY(h_extremes(c, c->st.h, hb, hmin, hmax));
@@ -803,6 +916,9 @@ void sph_destroy(sph_ctx *c) {
   for (void *p : c->owned) cudaFree(p);
   if (c->ctr) cudaFree(c->ctr);
   if (c->ctr_h) cudaFreeHost(c->ctr_h);
+  for (auto &pair : c->ev)
+    for (auto &e : pair)
+      if (e) cudaEventDestroy(e);
   delete c;
 }
 

@@ -12,6 +12,13 @@
 
 namespace sph {
 
+// Kernel-launch counter of the context whose API call is running on this
+// thread (set at API entry); every launch wrapper adds its launches.
+extern thread_local long long *g_launch_count;
+inline void note_launch(int k = 1) {
+  if (g_launch_count) *g_launch_count += k;
+}
+
 constexpr int kMaxDepth = 10;   // octree levels below a top cell (1024 sub-cells per edge)
 constexpr int kWarp = 32;
 constexpr float kInvPi = 0.318309886183790671538f;

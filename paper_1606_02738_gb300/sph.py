@@ -44,7 +44,8 @@ class sph_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("n_ngb", ctypes.c_double),
                 ("h_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("n_split", ctypes.c_int), ("precision", ctypes.c_int),
-                ("mode", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("mode", ctypes.c_int), ("profile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -56,7 +57,14 @@ class sph_stats_t(ctypes.Structure):
                 ("force_pair_candidates", ctypes.c_int64),
                 ("density_passes", ctypes.c_int32), ("rebuilds", ctypes.c_int32),
                 ("max_iter_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("h_min", ctypes.c_double), ("h_max", ctypes.c_double)]
+                ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("total_density_interactions", ctypes.c_int64),
+                ("total_force_interactions", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("density_launches", ctypes.c_int64),
+                ("force_launches", ctypes.c_int64),
+                ("t_grid_ms", ctypes.c_double), ("t_lists_ms", ctypes.c_double),
+                ("t_density_ms", ctypes.c_double), ("t_ghost_ms", ctypes.c_double),
+                ("t_force_ms", ctypes.c_double), ("t_integrate_ms", ctypes.c_double)]
 
 
 class SphError(RuntimeError):
@@ -213,12 +221,14 @@ class Context:
 
     def __init__(self, n_split: int = 64, precision: int = SPH_PREC_FP32,
                  mode: int = SPH_MODE_PLAIN, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
-                 h_tol: float = 1e-6, max_iter: int = 30, stream=None, device="cuda"):
+                 h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False, stream=None,
+                 device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         p = sph_default_params()
         p.n_split, p.precision, p.mode = n_split, precision, mode
+        p.profile = int(bool(profile))
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream

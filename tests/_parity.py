@@ -49,7 +49,7 @@ def edge_pairs(s, factor=EDGE):
     return amb
 
 
-def compare_density(g, s, tol_rho=TOL_RHO, tol_h=TOL_H, counts=True):
+def compare_density(g, s, tol_rho=TOL_RHO, tol_h=TOL_H, counts=True, check_P=True):
     err = {}
     err["h"] = np.max(np.abs(g["h"] / s.h - 1))
     err["rho"] = np.max(np.abs(g["rho"] / s.rho - 1))
@@ -59,7 +59,8 @@ def compare_density(g, s, tol_rho=TOL_RHO, tol_h=TOL_H, counts=True):
     assert err["h"] <= tol_h, err
     assert err["rho"] <= tol_rho, err
     assert err["omega"] <= TOL_OMEGA, err
-    assert err["P"] <= 2 * tol_rho, err
+    if check_P:  # after a step P uses the predicted u of the force evaluation
+        assert err["P"] <= 2 * tol_rho, err
     if counts:
         amb = edge_pairs(s)
         diff = np.abs(g["nngb"].astype(np.int64) - s.n_dens)
