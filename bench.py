@@ -350,7 +350,8 @@ def run_ours(args, d: Dist):
         e2e_inter += (sb["total_density_interactions"] - sa["total_density_interactions"] +
                       sb["total_force_interactions"] - sa["total_force_interactions"])
     e2e_ms_max = d.reduce(e2e_ms, "MAX")
-    e2e_val = d.reduce(float(e2e_inter), "SUM") / (e2e_ms_max / 1000.0)
+    e2e_val = (d.reduce(float(e2e_inter), "SUM") / (e2e_ms_max / 1000.0)
+               if e2e_ms_max > 0 else None)
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:

@@ -195,18 +195,20 @@ void launch_validate(const double *x, const float *v, const float *m, const floa
 }
 
 __global__ void k_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi,
-                                  int n) {
+                                  float *fprev, int n) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   done[s] = 0;
   niter[s] = 0;
   hlo[s] = 0.0;
   hhi[s] = 1e308;
+  fprev[s] = __int_as_float(0x7f800000);
 }
 
-void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi, int n,
-                            cudaStream_t s) {
-  k_reset_iteration<<<(n + 255) / 256, 256, 0, s>>>(done, niter, hlo, hhi, n); note_launch();
+void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi,
+                            float *fprev, int n, cudaStream_t s) {
+  k_reset_iteration<<<(n + 255) / 256, 256, 0, s>>>(done, niter, hlo, hhi, fprev, n);
+  note_launch();
 }
 
 __global__ void k_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of) {

@@ -155,15 +155,17 @@ __global__ void k_ghost(GhostArgs a) {
         lo = h;
       else
         hi = h;
-      double hn;
-      if (fabs(f) > 0.25 * a.n_ngb || !(dN > 0.0)) {
-        // far from the root: N ~ h^3 locally, so rescale h by (n_ngb / N)^(1/3)
-        hn = h * cbrt(a.n_ngb / N);
-      } else {
-        hn = h - f / dN;  // Newton
-      }
-      hn = fmin(fmax(hn, 0.5 * h), 2.0 * h);
-      if (hi < 1e300 && !(hn > lo && hn < hi)) hn = 0.5 * (lo + hi);
+      // Newton on ln N(ln h): N grows like a power of h whose exponent
+      // s = d ln N / d ln h = h N' / N is measured, not assumed (near
+      // clusters s >> 3). No neighbour besides i itself (N' = 0): double h.
+      const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
+      double hn = s_ln > 0.0 ? h * exp(log(a.n_ngb / N) / s_ln) : 2.0 * h;
+      hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
+      // safeguard: bisect the bracket when the step leaves it or |f| did not
+      // at least halve since the previous pass
+      const double fprev = (double)a.fprev[i];
+      if (hi < 1e300 && (!(hn > lo && hn < hi) || fabs(f) > 0.5 * fprev)) hn = 0.5 * (lo + hi);
+      a.fprev[i] = (float)fabs(f);
       const Leaf &L = a.leaves[a.leaf_of[i]];
       const BoxDev &B = a.boxes[L.box];
       const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
@@ -174,8 +176,8 @@ __global__ void k_ghost(GhostArgs a) {
         if (h >= hcap * (1.0 - 1e-12) && f < 0.0) st |= kErrBoxTooSmall;
         hn = hcap;
       }
-      if (fabs(hn - h) <= 1e-7 * h && !(st & kErrBoxTooSmall)) {
-        conv = true;  // below the resolution of the FP32 sums: keep h
+      if (fabs(hn - h) <= 5e-7 * h && !(st & kErrBoxTooSmall)) {
+        conv = true;  // h within 5e-7 of the root (FP32-sum resolution): keep h
       } else {
         a.h[i] = hn;
         a.hf[i] = (float)hn;

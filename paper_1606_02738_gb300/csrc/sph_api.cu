@@ -57,7 +57,7 @@ struct sph_ctx {
   float4 *pm = nullptr, *sums = nullptr, *fi = nullptr;
   int *cnt = nullptr, *niter = nullptr, *nngb = nullptr, *nforce = nullptr, *leaf_of = nullptr;
   unsigned char *done = nullptr;
-  float *rho = nullptr, *omega = nullptr, *P = nullptr;
+  float *rho = nullptr, *omega = nullptr, *P = nullptr, *fprev = nullptr;
   int *cell_of = nullptr, *order = nullptr, *order_tmp = nullptr, *flag = nullptr,
       *excl = nullptr, *ident = nullptr;
   unsigned *mkey = nullptr, *msrt = nullptr, *mscr = nullptr;
@@ -205,7 +205,7 @@ FixedLayout fixed_layout(int64_t n, int nb) {
   add(N * sizeof(float4));         // fi
   for (int k = 0; k < 5; ++k) add(N * sizeof(int));  // cnt niter nngb nforce leaf_of
   add(N);                          // done
-  for (int k = 0; k < 3; ++k) add(N * sizeof(float));  // rho omega P
+  for (int k = 0; k < 4; ++k) add(N * sizeof(float));  // rho omega P fprev
   add(N * sizeof(int));            // cell_of
   add(N * sizeof(int));            // order
   add(N * sizeof(int));            // order_tmp
@@ -272,6 +272,7 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   take(c->rho);
   take(c->omega);
   take(c->P);
+  take(c->fprev);
   take(c->cell_of);
   take(c->order);
   take(c->order_tmp);
@@ -566,7 +567,7 @@ int check_status(sph_ctx *c, int st) {
 int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   if (!c->grid_valid) TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
   const int n = c->n;
-  launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, n, c->stream);
+  launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   c->last_passes = 0;
   c->last_rebuilds = 0;
@@ -619,6 +620,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
     gh.h = c->st.h;
     gh.hlo = c->st.hlo;
     gh.hhi = c->st.hhi;
+    gh.fprev = c->fprev;
     gh.hf = c->hf;
     gh.sums = c->sums;
     gh.cnt = c->cnt;
@@ -642,7 +644,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
       // an h outgrew its top cell: regrid with the current h and start the
       // converged bookkeeping again (the per-particle results are reordered)
       TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
-      launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, n, c->stream);
+      launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
       CUDA_TRY(cudaMemsetAsync(&c->ctr->dens_inter, 0, sizeof(unsigned long long), c->stream));
       ++c->last_rebuilds;
       continue;

@@ -163,8 +163,8 @@ void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
                        unsigned long long *dmax, unsigned long long *dminmax, cudaStream_t s);
 void launch_validate(const double *x, const float *v, const float *m, const float *u,
                      const double *h, int n, int *status, cudaStream_t s);
-void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi, int n,
-                            cudaStream_t s);
+void launch_reset_iteration(unsigned char *done, int *niter, double *hlo, double *hhi,
+                            float *fprev, int n, cudaStream_t s);
 
 struct ListArgs {
   int n_leaves;
@@ -212,6 +212,7 @@ struct GhostArgs {
   float cap_factor;
   double *h;
   double *hlo, *hhi;
+  float *fprev;           // |N - n_ngb| of the previous pass (step safeguard)
   float *hf;
   const float4 *sums;
   const int *cnt;

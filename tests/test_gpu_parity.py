@@ -130,12 +130,12 @@ def test_error_codes():
         c.density()
     assert e.value.code == sph.SPH_EBOXTOOSMALL
     c.close()
-    q = inputs.uniform(500, seed=2)
+    q = inputs.uniform(2000, seed=2)
     q.m[3] = -1.0
     with pytest.raises(SphError) as e:
         Context().load(q)
     assert e.value.code == sph.SPH_EINVAL
-    q = inputs.uniform(500, seed=2)
+    q = inputs.uniform(2000, seed=2)
     c = Context().load(q)
     with pytest.raises(SphError) as e:
         c.force()
