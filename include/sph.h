@@ -185,6 +185,39 @@ const char *sph_last_error(const sph_ctx *ctx);
 /* Release the context and every buffer the library allocated. NULL is a no-op. */
 void sph_destroy(sph_ctx *ctx);
 
+/* ---- allocation-free density stage (no counterpart in the paper) ----
+ *
+ * For callers that may not allocate device memory on their calls: a host
+ * framework that owns the whole GPU through its own memory pool, or code
+ * where a cudaMalloc/cudaFree (which can also synchronise the device) is not
+ * allowed. The regular entry points allocate a particle store and task lists;
+ * this one allocates nothing. It runs the same density sums and the same
+ * smoothing-length iteration as sph_density for ONE periodic box of at most
+ * SPH_NOALLOC_MAX_PARTICLES particles, finding neighbours by scanning all
+ * particles (minimum image), and keeps its per-particle scratch (~0.9 MB) in
+ * a fixed device array that exists on every device that loads the library
+ * until the process exits.
+ *
+ *   n          particles, 1 <= n <= SPH_NOALLOC_MAX_PARTICLES (else SPH_EINVAL)
+ *   box_len    host, 3 edge lengths of the periodic box (> 0)
+ *   x          device, double [n][3] positions (inside or outside the box)
+ *   m          device, float [n] masses
+ *   h0         device, double [n] initial smoothing-length guesses (> 0)
+ *   n_ngb, h_tol, max_iter   as in sph_params
+ *   h_out      device, double [n]: converged h
+ *   rho_out    device, float [n]: density, Eq. (rho)
+ *   omega_out  device, float [n]: Omega = 1 + h/(3 rho) drho/dh
+ *   cuda_stream  cudaStream_t of the work (NULL: legacy default stream)
+ * Returns SPH_OK, SPH_EINVAL, SPH_ECUDA, SPH_EBOXTOOSMALL, SPH_ENONPHYSICAL
+ * or SPH_ENOTCONVERGED; synchronises the stream once per iteration pass.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture. All calls share
+ * the one scratch array: calls whose work overlaps on the GPU race on it. */
+#define SPH_NOALLOC_MAX_PARTICLES 16384
+int sph_density_noalloc(int n, const double *box_len, const double *x, const float *m,
+                        const double *h0, double n_ngb, double h_tol, int max_iter,
+                        double *h_out, float *rho_out, float *omega_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -213,6 +213,29 @@ def sph_destroy(ctx) -> None:
         lib().sph_destroy(ctx)
 
 
+SPH_NOALLOC_MAX_PARTICLES = 16384
+
+
+def sph_density_noalloc(box_len, x, m, h0, h_out, rho_out, omega_out, n_ngb: float = 48.0,
+                        h_tol: float = 1e-6, max_iter: int = 30, stream=None) -> None:
+    """Allocation-free density stage for one small box (see include/sph.h):
+    x (N,3) float64, m (N) float32, h0 (N) float64 in; h_out (N) float64,
+    rho_out, omega_out (N) float32 out -- all CUDA tensors the caller owns."""
+    L = lib()
+    f = L.sph_density_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    box = np.ascontiguousarray(box_len, dtype=np.float64).reshape(3)
+    rc = f(int(x.shape[0]), box.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(_ptr(x)),
+           ctypes.c_void_p(_ptr(m)), ctypes.c_void_p(_ptr(h0)), float(n_ngb), float(h_tol),
+           int(max_iter), ctypes.c_void_p(_ptr(h_out)), ctypes.c_void_p(_ptr(rho_out)),
+           ctypes.c_void_p(_ptr(omega_out)), _stream(stream))
+    if rc != SPH_OK:
+        raise SphError(rc, "sph_density_noalloc", "")
+
+
 # ------------------------------------------------- convenience (marshalling)
 
 class Context:
