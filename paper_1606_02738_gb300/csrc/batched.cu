@@ -1,0 +1,575 @@
+// batched.cu -- the batched interaction form: one warp per target group of up
+// to 32 consecutive particles of a top cell, candidates staged once in shared
+// memory, per-lane compacted neighbour lists, and the smoothing-length
+// iteration run inside the kernel (Section 2 density and force, with the
+// ghost task of Section 3.1 fused into the density kernel).
+//
+// Per group:
+//   1. walk the octrees of the 27 neighbouring top cells for the source leaves
+//      whose box lies within the group's radius (the refined pair tasks);
+//   2. stage, into shared memory, every source particle within that radius of
+//      the group's bounding box, shifted into the group's frame (one test per
+//      candidate per warp);
+//   3. each lane keeps the staged particles within its own radius in a list of
+//      16-bit indices, so the passes over h, and the force, touch only those;
+//   4. density: sums, FP64 Newton step on ln N(ln h), repeat until every lane
+//      converged (list rebuilt from the stage when an h outgrows it);
+//      force: one pass over the list.
+// A group whose candidates overflow the shared-memory stage, or whose h
+// outgrows the staged radius, is left to the per-pass form (the host runs it
+// for every particle not finished here), so results never depend on the
+// capacities.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kGroup = 32;
+constexpr int kBW = 2;          // warps per block
+constexpr int kStageD = 1024;   // density stage capacity (particles)
+constexpr int kStageF = 512;    // force stage capacity
+constexpr int kListMax = 128;   // per-lane list capacity
+constexpr int kWalkStack = 96;
+
+__device__ __forceinline__ int box_of_cell_b(const BoxDev *b, int nb, int c) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b[mid].cell_base <= c)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void cell_xyz(const BoxDev &B, int local, int c[3]) {
+  c[2] = local % B.n[2];
+  c[1] = (local / B.n[2]) % B.n[1];
+  c[0] = local / (B.n[1] * B.n[2]);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_max_int(int v) {
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void add_comp(float &s, float &c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- groups
+
+__global__ void k_group_count(GroupBuildArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < a.n_cells) a.gcount[c] = (a.cell_count[c] + kGroup - 1) / kGroup;
+}
+
+void launch_group_count(const GroupBuildArgs &a, cudaStream_t s) {
+  k_group_count<<<(a.n_cells + 255) / 256, 256, 0, s>>>(a);
+  note_launch();
+}
+
+// gcount holds the exclusive offsets here.
+__global__ void k_group_fill(GroupBuildArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.n_cells) return;
+  const int cnt = a.cell_count[c], first = a.gcount[c];
+  const int box = box_of_cell_b(a.boxes, a.n_boxes, c);
+  for (int k = 0; k * kGroup < cnt; ++k) {
+    Group G;
+    G.start = a.cell_start[c] + k * kGroup;
+    G.count = min(kGroup, cnt - k * kGroup);
+    G.cell = c;
+    G.box = box;
+    for (int d = 0; d < 3; ++d) {
+      G.o[d] = 0.0;
+      G.tlo[d] = G.thi[d] = G.flo[d] = G.fhi[d] = 0.f;
+    }
+    G.hmax = 0.f;
+    G.pad = 0;
+    a.groups[first + k] = G;
+  }
+}
+
+void launch_group_fill(const GroupBuildArgs &a, cudaStream_t s) {
+  k_group_fill<<<(a.n_cells + 255) / 256, 256, 0, s>>>(a);
+  note_launch();
+}
+
+// One warp per group: frame origin (leaf-cell origin of its first particle)
+// and the bounding boxes in the group frame and relative to the top cell.
+__global__ void k_group_geometry(GroupBuildArgs a) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= a.n_groups) return;
+  Group *G = &a.groups[g];
+  const int start = G->start, count = G->count;
+  const Leaf &L0 = a.leaves[a.leaf_of[start]];
+  const double o[3] = {L0.o[0], L0.o[1], L0.o[2]};
+  float flo[3] = {3e38f, 3e38f, 3e38f}, fhi[3] = {-3e38f, -3e38f, -3e38f};
+  float tlo[3] = {3e38f, 3e38f, 3e38f}, thi[3] = {0.f, 0.f, 0.f};
+  if (lane < count) {
+    const int i = start + lane;
+    const Leaf &L = a.leaves[a.leaf_of[i]];
+    const float4 q = a.pm[i];
+    const float pq[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float f = pq[d] + (float)(L.o[d] - o[d]);
+      const float t = fmaxf((float)(L.o[d] + (double)pq[d]), 0.f);
+      flo[d] = fhi[d] = f;
+      tlo[d] = thi[d] = t;
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int s = 16; s; s >>= 1) {
+      flo[d] = fminf(flo[d], __shfl_xor_sync(0xffffffffu, flo[d], s));
+      fhi[d] = fmaxf(fhi[d], __shfl_xor_sync(0xffffffffu, fhi[d], s));
+      tlo[d] = fminf(tlo[d], __shfl_xor_sync(0xffffffffu, tlo[d], s));
+      thi[d] = fmaxf(thi[d], __shfl_xor_sync(0xffffffffu, thi[d], s));
+    }
+  if (lane == 0) {
+    for (int d = 0; d < 3; ++d) {
+      G->o[d] = o[d];
+      G->flo[d] = flo[d];
+      G->fhi[d] = fhi[d];
+      G->tlo[d] = tlo[d];
+      G->thi[d] = thi[d];
+    }
+  }
+}
+
+void launch_group_geometry(const GroupBuildArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  k_group_geometry<<<(a.n_groups * 32 + 255) / 256, 256, 0, s>>>(a);
+  note_launch();
+}
+
+__global__ void k_group_hmax(GroupBuildArgs a) {
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= a.n_groups) return;
+  Group *G = &a.groups[g];
+  float hm = lane < G->count ? a.hf[G->start + lane] : 0.f;
+  for (int s = 16; s; s >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, s));
+  if (lane == 0) G->hmax = hm;
+}
+
+void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  k_group_hmax<<<(a.n_groups * 32 + 255) / 256, 256, 0, s>>>(a);
+  note_launch();
+}
+
+// One thread per group: the source leaves within the group's radius, found by
+// walking the octrees of the 27 neighbouring top cells (periodic). Count pass
+// when a.tasks is null, fill pass otherwise.
+__global__ void k_group_lists(GroupListArgs a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_groups) return;
+  const Group G = a.groups[g];
+  const BoxDev &B = a.boxes[G.box];
+  int c[3];
+  cell_xyz(B, G.cell - B.cell_base, c);
+  const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
+  const float capG = a.force ? G.hmax : fminf(G.hmax * a.skin, wmin);
+  const bool fill = a.tasks != nullptr;
+  const int base = fill ? a.offset[g] : 0;
+  int cnt = 0;
+  int stack[kWalkStack];
+  for (int dx = -1; dx <= 1; ++dx)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                           (c[2] + dz + B.n[2]) % B.n[2]};
+        const int cellS = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+        const double shd[3] = {dx * B.w[0], dy * B.w[1], dz * B.w[2]};
+        const float sh[3] = {(float)shd[0], (float)shd[1], (float)shd[2]};
+        int top = 0;
+        stack[top++] = cellS;
+        while (top > 0) {
+          const int id = stack[--top];
+          const Node &S = a.nodes[id];
+          if (S.count == 0) continue;
+          float d2 = 0.f;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float gap = fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - G.thi[d], G.tlo[d] - S.hi[d] - sh[d]));
+            d2 = fmaf(gap, gap, d2);
+          }
+          const float crit = (a.force ? fmaxf(capG, S.hmax) : capG) + B.eps;
+          if (d2 >= crit * crit) continue;
+          if (S.child < 0) {
+            if (fill) {
+              const Leaf &LS = a.leaves[S.leaf];
+              Task tk;
+              tk.sx = (float)(LS.o[0] + shd[0] - G.o[0]);
+              tk.sy = (float)(LS.o[1] + shd[1] - G.o[1]);
+              tk.sz = (float)(LS.o[2] + shd[2] - G.o[2]);
+              tk.src = S.leaf;
+              a.tasks[base + cnt] = tk;
+            }
+            ++cnt;
+          } else if (top + 8 <= kWalkStack) {
+            for (int o = 7; o >= 0; --o) stack[top++] = S.child + o;
+          } else {
+            atomicOr(a.status, kErrListOverflow);
+          }
+        }
+      }
+  if (!fill) a.count[g] = cnt;
+}
+
+void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  k_group_lists<<<(a.n_groups + 127) / 128, 128, 0, s>>>(a);
+  note_launch();
+}
+
+// ------------------------------------------------------------ density
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
+  __shared__ float4 stage_all[kBW][kStageD];
+  __shared__ unsigned short list_all[kBW][kListMax * 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned ltmask = (1u << lane) - 1u;
+  float4 *stage = stage_all[warp];
+  unsigned short *list = list_all[warp];
+  unsigned long long cand = 0, inter = 0;
+  int fallback = 0, max_it = 0, st_bits = 0;
+
+  for (int g = blockIdx.x * kBW + warp; g < a.n_groups; g += gridDim.x * kBW) {
+    const Group G = a.groups[g];
+    const BoxDev &B = a.boxes[G.box];
+    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
+    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    const bool has = lane < G.count;
+    const int i = G.start + lane;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    HIter it;
+    it.h = 1.0;
+    it.lo = 0.0;
+    it.hi = 1e308;
+    it.fprev = __int_as_float(0x7f800000);
+    if (has) {
+      const Leaf &L = a.leaves[a.leaf_of[i]];
+      const float4 q = a.pm[i];
+      px = q.x + (float)(L.o[0] - G.o[0]);
+      py = q.y + (float)(L.o[1] - G.o[1]);
+      pz = q.z + (float)(L.o[2] - G.o[2]);
+      it.h = a.h[i];
+    }
+    const float Rg = fminf(G.hmax * a.skin_stage, wmin);
+    const float Rg2 = Rg * Rg;
+
+    // stage the candidates within Rg of the group box
+    int nst = 0;
+    const int e0 = a.off[g], e1 = a.off[g + 1];
+    for (int e = e0; e < e1; ++e) {
+      const Task tk = a.tasks[e];
+      const Leaf &LS = a.leaves[tk.src];
+      const int js = LS.start, jn = LS.count;
+      for (int jb = 0; jb < jn; jb += 32) {
+        bool in = false;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (jb + lane < jn) {
+          q = a.pm[js + jb + lane];
+          q.x += tk.sx;
+          q.y += tk.sy;
+          q.z += tk.sz;
+          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
+          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
+          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
+          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < Rg2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        const int pos = nst + __popc(m & ltmask);
+        if (in && pos < kStageD) stage[pos] = q;
+        nst += __popc(m);
+      }
+    }
+    __syncwarp();
+    bool failed = nst > kStageD;
+
+    bool fin = !has;
+    bool need = has;
+    int cnt = 0, passes = 0, ngb = 0;
+    float rl = 0.f;
+    float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pass = 0; !failed && pass < a.max_iter; ++pass) {
+      // (re)build the lists of lanes whose h outgrew their list radius
+      const bool bld = need && !fin;
+      if (__any_sync(0xffffffffu, bld)) {
+        float rl2 = -1.f;
+        if (bld) {
+          rl = fminf((float)it.h * a.skin_list, Rg);
+          rl2 = rl * rl;
+          cnt = 0;
+          cand += nst;
+        }
+        for (int k = 0; k < nst; ++k) {
+          const float4 q = stage[k];
+          const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < rl2) {
+            if (cnt < kListMax) list[cnt * 32 + lane] = (unsigned short)k;
+            ++cnt;
+          }
+        }
+        need = false;
+        if (__any_sync(0xffffffffu, cnt > kListMax)) {
+          failed = true;
+          break;
+        }
+        __syncwarp();
+      }
+      // sums at the current h
+      const float hf = (float)it.h;
+      const float h2 = fin ? -1.f : hf * hf;
+      const float hinv = 1.f / hf;
+      float sw = 0.f, sdw = 0.f, smw = 0.f, smdh = 0.f;
+      float cw = 0.f, cdw = 0.f, cmw = 0.f, cmdh = 0.f;
+      int c = 0;
+      const int tmax = warp_max_int(fin ? 0 : cnt);
+      for (int t = 0; t < tmax; ++t) {
+        if (t < cnt && !fin) {
+          const float4 q = stage[list[t * 32 + lane]];
+          const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (r2 < h2) {
+            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+            const float qq = r * hinv;
+            float w, dw;
+            w_and_dw(qq, w, dw);
+            const float qdw = qq * dw;
+            if (KAHAN) {
+              add_comp(sw, cw, w);
+              add_comp(sdw, cdw, qdw);
+              add_comp(smw, cmw, q.w * w);
+              add_comp(smdh, cmdh, q.w * fmaf(3.f, w, qdw));
+            } else {
+              sw += w;
+              sdw += qdw;
+              smw = fmaf(q.w, w, smw);
+              smdh = fmaf(q.w, fmaf(3.f, w, qdw), smdh);
+            }
+            ++c;
+          }
+        }
+      }
+      if (!fin) {
+        cand += cnt;
+        ++passes;
+        int st = 0;
+        const bool conv = h_newton_step(it, sw, sdw, a.n_ngb, a.tol, hcap, &st);
+        st_bits |= st;
+        if (conv) {
+          fin = true;
+          fs = make_float4(sw, sdw, smw, smdh);
+          ngb = c - 1;  // the self term is always inside
+        } else if ((float)it.h > rl) {
+          need = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rg)) failed = true;  // beyond the stage
+      if (__all_sync(0xffffffffu, fin)) break;
+    }
+    if (failed || !__all_sync(0xffffffffu, fin)) {
+      // left to the per-pass form: keep the incoming h and flags
+      if (has) ++fallback;
+      continue;
+    }
+    if (has) {
+      float rho, omega, P;
+      float4 fi;
+      const bool ok = finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi);
+      if (!ok) st_bits |= kErrNonPhysical;
+      a.h[i] = it.h;
+      a.hf[i] = (float)it.h;
+      a.rho[i] = rho;
+      a.omega[i] = omega;
+      a.P[i] = P;
+      a.fi[i] = fi;
+      a.nngb[i] = ngb;
+      a.niter[i] = passes;
+      a.done[i] = 1;
+      inter += (unsigned long long)ngb;
+      max_it = max(max_it, passes);
+    }
+  }
+  cand = warp_sum(cand);
+  inter = warp_sum(inter);
+  fallback = (int)warp_sum((unsigned long long)fallback);
+  max_it = warp_max_int(max_it);
+  for (int o = 16; o; o >>= 1) st_bits |= __shfl_xor_sync(0xffffffffu, st_bits, o);
+  if (lane == 0) {
+    if (cand) atomicAdd(&a.ctr->dens_cand, cand);
+    if (inter) atomicAdd(&a.ctr->dens_inter, inter);
+    if (fallback) atomicAdd(&a.ctr->unconverged, fallback);
+    if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
+    if (st_bits) atomicOr(&a.ctr->status, st_bits);
+  }
+}
+
+void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  int blocks = (a.n_groups + kBW - 1) / kBW;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (a.kahan)
+    k_density_batched<true><<<blocks, kBW * 32, 0, s>>>(a);
+  else
+    k_density_batched<false><<<blocks, kBW * 32, 0, s>>>(a);
+  note_launch();
+}
+
+// -------------------------------------------------------------- force
+
+__global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
+  __shared__ float4 sq_all[kBW][kStageF];   // position in the group frame, m
+  __shared__ float4 sf_all[kBW][kStageF];   // h, 1/h, A (8/pi) h^-4, global index
+  __shared__ unsigned short list_all[kBW][kListMax * 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned ltmask = (1u << lane) - 1u;
+  float4 *sq = sq_all[warp];
+  float4 *sf = sf_all[warp];
+  unsigned short *list = list_all[warp];
+  unsigned long long cand = 0, inter = 0;
+  int fallback = 0;
+
+  for (int g = blockIdx.x * kBW + warp; g < a.n_groups; g += gridDim.x * kBW) {
+    const Group G = a.groups[g];
+    const bool has = lane < G.count;
+    const int i = G.start + lane;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    float4 fi = make_float4(1.f, 1.f, 0.f, -1.f), vi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (has) {
+      const Leaf &L = a.leaves[a.leaf_of[i]];
+      const float4 q = a.pm[i];
+      px = q.x + (float)(L.o[0] - G.o[0]);
+      py = q.y + (float)(L.o[1] - G.o[1]);
+      pz = q.z + (float)(L.o[2] - G.o[2]);
+      fi = a.fi[i];
+      vi = a.vu[i];
+    }
+    const float hi2 = has ? fi.x * fi.x : -1.f;
+
+    // stage: j within max(hmax_G, h_j) of the group box
+    int nst = 0;
+    const int e0 = a.off[g], e1 = a.off[g + 1];
+    for (int e = e0; e < e1; ++e) {
+      const Task tk = a.tasks[e];
+      const Leaf &LS = a.leaves[tk.src];
+      const int js = LS.start, jn = LS.count;
+      for (int jb = 0; jb < jn; jb += 32) {
+        bool in = false;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q;
+        const int j = js + jb + lane;
+        if (jb + lane < jn) {
+          q = a.pm[j];
+          f = a.fi[j];
+          q.x += tk.sx;
+          q.y += tk.sy;
+          q.z += tk.sz;
+          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
+          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
+          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
+          const float R = fmaxf(G.hmax, f.x);
+          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        const int pos = nst + __popc(m & ltmask);
+        if (in && pos < kStageF) {
+          sq[pos] = q;
+          sf[pos] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+        }
+        nst += __popc(m);
+      }
+    }
+    __syncwarp();
+    bool failed = nst > kStageF;
+    int cnt = 0;
+    if (!failed) {
+      for (int k = 0; k < nst; ++k) {
+        const float4 q = sq[k];
+        const float hj = sf[k].x;
+        const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj * hj)) {
+          if (cnt < kListMax) list[cnt * 32 + lane] = (unsigned short)k;
+          ++cnt;
+        }
+      }
+      if (has) cand += nst;
+      failed = __any_sync(0xffffffffu, cnt > kListMax);
+      __syncwarp();
+    }
+    if (failed) {
+      if (has) ++fallback;
+      continue;
+    }
+    float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+    const int tmax = warp_max_int(has ? cnt : 0);
+    for (int t = 0; t < tmax; ++t) {
+      if (t < cnt) {
+        const int k = list[t * 32 + lane];
+        const float4 q = sq[k];
+        const float4 f = sf[k];
+        const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
+        const float tj = f.z * dw_only(r * f.y);    // A_j dW/dr(r, h_j)
+        const float fac = q.w * (ti + tj) * rinv;
+        const float4 vj = a.vu[__float_as_int(f.w)];
+        const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+        ax = fmaf(-fac, dx, ax);
+        ay = fmaf(-fac, dy, ay);
+        az = fmaf(-fac, dz, az);
+        du = fmaf(q.w * ti * rinv, dvdx, du);
+      }
+    }
+    if (has) {
+      a.acc[i] = make_float4(ax, ay, az, du);
+      a.nforce[i] = cnt;
+      a.fdone[i] = 1;
+      inter += (unsigned long long)cnt;
+      cand += cnt;
+    }
+  }
+  cand = warp_sum(cand);
+  inter = warp_sum(inter);
+  fallback = (int)warp_sum((unsigned long long)fallback);
+  if (lane == 0) {
+    if (cand) atomicAdd(&a.ctr->force_cand, cand);
+    if (inter) atomicAdd(&a.ctr->force_inter, inter);
+    if (fallback) atomicAdd(&a.ctr->unconverged, fallback);
+  }
+}
+
+void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  int blocks = (a.n_groups + kBW - 1) / kBW;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_force_batched<<<blocks, kBW * 32, 0, s>>>(a);
+  note_launch();
+}
+
+}  // namespace sph

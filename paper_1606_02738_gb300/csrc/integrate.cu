@@ -163,19 +163,60 @@ void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
   k_h_to_float<<<(n + 255) / 256, 256, 0, s>>>(h, hf, n); note_launch();
 }
 
+constexpr int kExtItems = 8;
+
+// Non-negative doubles order like their bit patterns, so the extremes are
+// reduced on the bits. Each thread takes kExtItems consecutive slots, the
+// warp reduces, and one lane per warp issues the atomics (per-box maxima: one
+// atomic per warp when the whole warp lies in one box, else one per lane).
 __global__ void k_h_extremes(const double *h, int n, const BoxDev *boxes, int nb,
                              unsigned long long *dmax, unsigned long long *dminmax) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(h[s]);
-  atomicMax(&dmax[box_of_slot(boxes, nb, s)], b);
-  atomicMin(&dminmax[0], b);
-  atomicMax(&dminmax[1], b);
+  const int lane = threadIdx.x & 31;
+  const int base = (blockIdx.x * blockDim.x + threadIdx.x) * kExtItems;
+  unsigned long long mn = ~0ull, mx = 0ull, bmax = 0ull;
+  int box = -1;
+  for (int k = 0; k < kExtItems; ++k) {
+    const int s = base + k;
+    if (s >= n) break;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(h[s]);
+    mn = b < mn ? b : mn;
+    mx = b > mx ? b : mx;
+    const int bs = box_of_slot(boxes, nb, s);
+    if (bs != box) {
+      if (box >= 0) atomicMax(&dmax[box], bmax);
+      box = bs;
+      bmax = b;
+    } else if (b > bmax) {
+      bmax = b;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, mx, o);
+    mn = a < mn ? a : mn;
+    mx = c > mx ? c : mx;
+  }
+  if (lane == 0 && mx > 0ull) {
+    atomicMin(&dminmax[0], mn);
+    atomicMax(&dminmax[1], mx);
+  }
+  const int box0 = __shfl_sync(0xffffffffu, box, 0);
+  if (__all_sync(0xffffffffu, box == box0 || box < 0)) {
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long c = __shfl_xor_sync(0xffffffffu, bmax, o);
+      bmax = c > bmax ? c : bmax;
+    }
+    if (lane == 0 && box0 >= 0) atomicMax(&dmax[box0], bmax);
+  } else if (box >= 0) {
+    atomicMax(&dmax[box], bmax);
+  }
 }
 
 void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
                        unsigned long long *dmax, unsigned long long *dminmax, cudaStream_t s) {
-  k_h_extremes<<<(n + 255) / 256, 256, 0, s>>>(h, n, boxes, n_boxes, dmax, dminmax); note_launch();
+  const int threads = (n + kExtItems - 1) / kExtItems;
+  k_h_extremes<<<(threads + 255) / 256, 256, 0, s>>>(h, n, boxes, n_boxes, dmax, dminmax);
+  note_launch();
 }
 
 __global__ void k_validate(const double *x, const float *v, const float *m, const float *u,

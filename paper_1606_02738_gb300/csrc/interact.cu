@@ -141,75 +141,46 @@ __global__ void k_ghost(GhostArgs a) {
   bool finished_now = false;
   int ngb = 0;
   if (i < a.n && !a.done[i]) {
-    const double h = a.h[i];
     const float4 s = a.sums[i];
-    const double N = (32.0 / 3.0) * (double)s.x;
-    const double dN = -(32.0 / (3.0 * h)) * (double)s.y;
-    const double f = N - a.n_ngb;
     const int it = a.niter[i] + 1;
     a.niter[i] = it;
-    bool conv = fabs(f) <= a.tol * a.n_ngb;
+    HIter hs;
+    hs.h = a.h[i];
+    hs.lo = a.hlo[i];
+    hs.hi = a.hhi[i];
+    hs.fprev = a.fprev[i];
+    const Leaf &L = a.leaves[a.leaf_of[i]];
+    const BoxDev &B = a.boxes[L.box];
+    const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
+    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    int st = 0;
+    const double h = hs.h;
+    const bool conv = h_newton_step(hs, s.x, s.y, a.n_ngb, a.tol, hcap, &st);
     if (!conv) {
-      double lo = a.hlo[i], hi = a.hhi[i];
-      if (f < 0.0)
-        lo = h;
-      else
-        hi = h;
-      // Newton on ln N(ln h): N grows like a power of h whose exponent
-      // s = d ln N / d ln h = h N' / N is measured, not assumed (near
-      // clusters s >> 3). No neighbour besides i itself (N' = 0): double h.
-      const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
-      double hn = s_ln > 0.0 ? h * exp(log(a.n_ngb / N) / s_ln) : 2.0 * h;
-      hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
-      // safeguard: bisect the bracket when the step leaves it or |f| did not
-      // at least halve since the previous pass
-      const double fprev = (double)a.fprev[i];
-      if (hi < 1e300 && (!(hn > lo && hn < hi) || fabs(f) > 0.5 * fprev)) hn = 0.5 * (lo + hi);
-      a.fprev[i] = (float)fabs(f);
-      const Leaf &L = a.leaves[a.leaf_of[i]];
-      const BoxDev &B = a.boxes[L.box];
-      const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
-      const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
-      int st = 0;
-      if (hn > hcap) {
-        // h may not exceed L/3: stop at the cap; a root beyond it is an error
-        if (h >= hcap * (1.0 - 1e-12) && f < 0.0) st |= kErrBoxTooSmall;
-        hn = hcap;
-      }
-      if (fabs(hn - h) <= 5e-7 * h && !(st & kErrBoxTooSmall)) {
-        conv = true;  // h within 5e-7 of the root (FP32-sum resolution): keep h
-      } else {
-        a.h[i] = hn;
-        a.hf[i] = (float)hn;
-        a.hlo[i] = lo;
-        a.hhi[i] = hi;
-        if (hn * (1.0 + 1e-6) > wmin) st |= kErrHGrid;
-        if (it >= a.max_iter) st |= kErrNotConverged;
-        atomicAdd(&a.ctr->unconverged, 1);
-      }
-      if (st) atomicOr(&a.ctr->status, st);
-    }
-    if (conv) {
-      const double h2 = h * h;
-      const double rho = 8.0 / 3.14159265358979323846 * (double)s.z / (h2 * h);
-      const double drho = -8.0 / 3.14159265358979323846 * (double)s.w / (h2 * h2);
-      const double omega = 1.0 + h / (3.0 * rho) * drho;
-      const double u = (double)a.vu[i].w;
-      const double P = (a.gamma - 1.0) * rho * u;
-      const double A = P / (omega * rho * rho);
-      a.rho[i] = (float)rho;
-      a.omega[i] = (float)omega;
-      a.P[i] = (float)P;
-      const float hf = (float)h;
-      a.force_i[i] = make_float4(hf, (float)(1.0 / h),
-                                 (float)(A * 8.0 / 3.14159265358979323846 / (h2 * h2)), hf * hf);
+      a.h[i] = hs.h;
+      a.hf[i] = (float)hs.h;
+      a.hlo[i] = hs.lo;
+      a.hhi[i] = hs.hi;
+      a.fprev[i] = hs.fprev;
+      if (hs.h * (1.0 + 1e-6) > wmin) st |= kErrHGrid;
+      if (it >= a.max_iter) st |= kErrNotConverged;
+      atomicAdd(&a.ctr->unconverged, 1);
+    } else {
+      float rho, omega, P;
+      float4 fi;
+      if (!finalise_density(h, s, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi))
+        st |= kErrNonPhysical;
+      a.rho[i] = rho;
+      a.omega[i] = omega;
+      a.P[i] = P;
+      a.force_i[i] = fi;
       a.done[i] = 1;
       a.nngb[i] = a.cnt[i];
       ngb = a.cnt[i];
       finished_now = true;
-      if (!(rho > 0.0) || !(omega > 0.0) || !(u >= 0.0)) atomicOr(&a.ctr->status, kErrNonPhysical);
       atomicMax(&a.ctr->max_iter_used, it);
     }
+    if (st) atomicOr(&a.ctr->status, st);
   }
   unsigned long long v = finished_now ? (unsigned long long)ngb : 0ull;
   v = warp_sum_u64(v);

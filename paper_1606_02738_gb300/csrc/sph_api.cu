@@ -56,7 +56,7 @@ struct sph_ctx {
   float *hf = nullptr;
   float4 *pm = nullptr, *sums = nullptr, *fi = nullptr;
   int *cnt = nullptr, *niter = nullptr, *nngb = nullptr, *nforce = nullptr, *leaf_of = nullptr;
-  unsigned char *done = nullptr;
+  unsigned char *done = nullptr, *fdone = nullptr;
   float *rho = nullptr, *omega = nullptr, *P = nullptr, *fprev = nullptr;
   int *cell_of = nullptr, *order = nullptr, *order_tmp = nullptr, *flag = nullptr,
       *excl = nullptr, *ident = nullptr;
@@ -65,6 +65,11 @@ struct sph_ctx {
   unsigned long long *hext = nullptr;  // per-box max h, then global min, max
 
   // growable, library-owned
+  // batched form: target groups and their task lists
+  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks;
+  int n_groups = 0;
+  bool groups_valid = false;
+  int64_t n_gd_tasks = 0, n_gf_tasks = 0;
   DevBuf cell_count, cell_start, cursor, nodes, frontier, frontier2, leaves, scan_tmp, active,
       dens_off, dens_tasks, force_off, force_tasks;
   int n_cells = 0, n_nodes = 0, n_leaves = 0;
@@ -205,6 +210,7 @@ FixedLayout fixed_layout(int64_t n, int nb) {
   add(N * sizeof(float4));         // fi
   for (int k = 0; k < 5; ++k) add(N * sizeof(int));  // cnt niter nngb nforce leaf_of
   add(N);                          // done
+  add(N);                          // fdone
   for (int k = 0; k < 4; ++k) add(N * sizeof(float));  // rho omega P fprev
   add(N * sizeof(int));            // cell_of
   add(N * sizeof(int));            // order
@@ -269,6 +275,7 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   take(c->nforce);
   take(c->leaf_of);
   take(c->done);
+  take(c->fdone);
   take(c->rho);
   take(c->omega);
   take(c->P);
@@ -494,6 +501,7 @@ int build_grid_inner(sph_ctx *c, bool from_caller, const float *cv, const float 
   launch_leaf_geometry(ga, n_nodes, c->stream);
   TRY(sync_check(c));
   c->grid_valid = true;
+  c->groups_valid = false;
   c->density_valid = false;
   c->force_valid = false;
   return SPH_OK;
@@ -564,6 +572,127 @@ int check_status(sph_ctx *c, int st) {
   return SPH_OK;
 }
 
+GroupBuildArgs group_args(sph_ctx *c) {
+  GroupBuildArgs ga{};
+  ga.n_cells = c->n_cells;
+  ga.cell_start = as<int>(c->cell_start);
+  ga.cell_count = as<int>(c->cell_count);
+  ga.boxes = c->boxes_d;
+  ga.n_boxes = c->nb;
+  ga.gcount = as<int>(c->gcount);
+  ga.groups = as<Group>(c->groups);
+  ga.n_groups = c->n_groups;
+  ga.leaves = as<Leaf>(c->leaves);
+  ga.leaf_of = c->leaf_of;
+  ga.pm = c->pm;
+  ga.hf = c->hf;
+  return ga;
+}
+
+// Target groups of the batched form: <= 32 consecutive particles per top cell.
+int build_groups(sph_ctx *c) {
+  const int C = c->n_cells;
+  TRY(ensure(c, c->gcount, sizeof(int) * (size_t)(C + 1)));
+  CUDA_TRY(cudaMemsetAsync(as<int>(c->gcount) + C, 0, sizeof(int), c->stream));
+  GroupBuildArgs ga = group_args(c);
+  launch_group_count(ga, c->stream);
+  exclusive_scan_int(ga.gcount, ga.gcount, C + 1, c->scan_tmp.p, c->scan_tmp.bytes, c->stream);
+  int ng = 0;
+  CUDA_TRY(cudaMemcpyAsync(&ng, ga.gcount + C, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->n_groups = ng;
+  TRY(ensure(c, c->groups, sizeof(Group) * (size_t)std::max(ng, 1)));
+  ga = group_args(c);
+  launch_group_fill(ga, c->stream);
+  launch_group_geometry(ga, c->stream);
+  c->groups_valid = true;
+  return sync_check(c);
+}
+
+// Group task lists: count pass, scan, fill pass.
+int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &off, DevBuf &tasks,
+                      int64_t &n_tasks) {
+  tic(c, kLists);
+  const int ng = c->n_groups;
+  TRY(ensure(c, off, sizeof(int) * (size_t)(ng + 1)));
+  GroupListArgs la{};
+  la.n_groups = ng;
+  la.groups = as<Group>(c->groups);
+  la.leaves = as<Leaf>(c->leaves);
+  la.nodes = as<Node>(c->nodes);
+  la.boxes = c->boxes_d;
+  la.force = force ? 1 : 0;
+  la.skin = skin;
+  la.count = as<int>(off);
+  la.status = &c->ctr->status;
+  CUDA_TRY(cudaMemsetAsync(as<int>(off) + ng, 0, sizeof(int), c->stream));
+  launch_group_lists(la, c->stream);
+  exclusive_scan_int(as<int>(off), as<int>(off), ng + 1, c->scan_tmp.p, c->scan_tmp.bytes,
+                     c->stream);
+  int total = 0;
+  CUDA_TRY(cudaMemcpyAsync(&total, as<int>(off) + ng, sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (total < 0) return fail(c, SPH_ENOMEM, "task list exceeds 2^31 entries");
+  TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(total, 1)));
+  la.offset = as<int>(off);
+  la.tasks = as<Task>(tasks);
+  launch_group_lists(la, c->stream);
+  n_tasks = total;
+  toc(c, kLists);
+  return sync_check(c);
+}
+
+constexpr float kSkinStage = 1.25f;  // staged radius = 1.25 x the group's largest h
+constexpr float kSkinList = 1.1f;    // per-lane list radius = 1.1 x the lane's h
+
+// Batched density: every particle whose group fits the stage and converges
+// inside the kernel is finished here; the rest keep done = 0 for the
+// per-pass loop.
+int density_batched(sph_ctx *c, const float4 *vu_for_P) {
+  if (!c->groups_valid) TRY(build_groups(c));
+  GroupBuildArgs ga = group_args(c);
+  launch_group_hmax(ga, c->stream);
+  GeomArgs gg = geom_args(c);
+  launch_leaf_hmax(gg, c->n_nodes, c->stream);
+  TRY(build_group_lists(c, false, kSkinStage, c->gd_off, c->gd_tasks, c->n_gd_tasks));
+  BatchDensArgs da{};
+  da.n_groups = c->n_groups;
+  da.groups = as<Group>(c->groups);
+  da.off = as<int>(c->gd_off);
+  da.tasks = as<Task>(c->gd_tasks);
+  da.leaves = as<Leaf>(c->leaves);
+  da.leaf_of = c->leaf_of;
+  da.pm = c->pm;
+  da.boxes = c->boxes_d;
+  da.h = c->st.h;
+  da.hf = c->hf;
+  da.vu = vu_for_P;
+  da.n_ngb = c->p.n_ngb;
+  da.tol = c->p.h_tol;
+  da.gamma = c->p.gamma;
+  da.max_iter = c->p.max_iter;
+  da.skin_stage = kSkinStage;
+  da.skin_list = kSkinList;
+  da.kahan = c->p.precision == SPH_PREC_KAHAN;
+  da.done = c->done;
+  da.niter = c->niter;
+  da.nngb = c->nngb;
+  da.rho = c->rho;
+  da.omega = c->omega;
+  da.P = c->P;
+  da.fi = c->fi;
+  da.ctr = c->ctr;
+  tic(c, kDens);
+  launch_density_batched(da, c->stream);
+  toc(c, kDens);
+  ++c->dens_launches;
+  TRY(read_counters(c));
+  TRY(check_status(c, c->ctr_h->status));
+  c->last_passes = c->ctr_h->max_iter_used;
+  return sync_check(c);
+}
+
 int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   if (!c->grid_valid) TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
   const int n = c->n;
@@ -571,6 +700,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   c->last_passes = 0;
   c->last_rebuilds = 0;
+  if (c->p.mode == SPH_MODE_BATCHED) TRY(density_batched(c, vu_for_P));
   const int max_passes = c->p.max_iter + 8;
   for (int pass = 0;; ++pass) {
     if (pass >= max_passes)
@@ -663,9 +793,57 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   return SPH_OK;
 }
 
+// Batched force; returns through *all_done whether every particle was
+// finished (else the per-leaf form must run).
+int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
+  *all_done = false;
+  if (!c->groups_valid) TRY(build_groups(c));
+  GroupBuildArgs gb = group_args(c);
+  launch_group_hmax(gb, c->stream);
+  GeomArgs ga = geom_args(c);
+  launch_leaf_hmax(ga, c->n_nodes, c->stream);
+  TRY(build_group_lists(c, true, 1.0f, c->gf_off, c->gf_tasks, c->n_gf_tasks));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
+  BatchForceArgs fa{};
+  fa.n_groups = c->n_groups;
+  fa.groups = as<Group>(c->groups);
+  fa.off = as<int>(c->gf_off);
+  fa.tasks = as<Task>(c->gf_tasks);
+  fa.leaves = as<Leaf>(c->leaves);
+  fa.leaf_of = c->leaf_of;
+  fa.pm = c->pm;
+  fa.fi = c->fi;
+  fa.vu = vu_for_force;
+  fa.acc = c->st.acc;
+  fa.nforce = c->nforce;
+  fa.fdone = c->fdone;
+  fa.ctr = c->ctr;
+  tic(c, kForce);
+  launch_force_batched(fa, c->stream);
+  toc(c, kForce);
+  ++c->force_launches;
+  c->force_pending = true;
+  TRY(read_counters(c));
+  *all_done = c->ctr_h->unconverged == 0;
+  if (*all_done)
+    c->force_valid = true;
+  else
+    c->total_force_inter -= c->ctr_h->force_inter;  // the per-leaf pass recounts all
+  return sync_check(c);
+}
+
 int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
   if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
+  if (c->p.mode == SPH_MODE_BATCHED && c->p.precision == SPH_PREC_FP32) {
+    bool all = false;
+    TRY(force_batched(c, vu_for_force, &all));
+    if (all) return SPH_OK;
+    // some group overflowed its stage: the per-leaf form recomputes every particle
+    TRY(read_counters(c));
+  }
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
   TRY(build_lists(c, true, nullptr, c->n_leaves, c->force_off, c->force_tasks,
@@ -913,7 +1091,8 @@ void sph_destroy(sph_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   DevBuf *bufs[] = {&c->cell_count, &c->cell_start, &c->cursor,   &c->nodes,      &c->frontier,
                     &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
-                    &c->dens_tasks, &c->force_off,  &c->force_tasks};
+                    &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
+                    &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks};
   for (DevBuf *b : bufs) release(*b);
   for (void *p : c->owned) cudaFree(p);
   if (c->ctr) cudaFree(c->ctr);

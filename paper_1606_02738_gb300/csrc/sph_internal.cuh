@@ -106,6 +106,86 @@ __device__ __forceinline__ float dw_only(float q) {
   return q < 1.f ? dw : 0.f;
 }
 
+// ---- one smoothing-length update (the ghost step, Section 2: the number of
+// neighbours is kept constant) shared by every density form ----
+struct HIter {
+  double h;      // current smoothing length
+  double lo, hi; // bracket: N(lo) < n_ngb <= N(hi); hi = 1e308 while open
+  float fprev;   // |N - n_ngb| of the previous pass
+};
+
+// Weighted neighbour number N = (32/3) sum w and dN/dh = -(32/(3h)) sum q w'
+// from the FP32 sums `s` at h. Returns true when h is accepted: |N - n_ngb| <=
+// tol n_ngb, or the next step would move h by at most 5e-7 h (the resolution
+// of FP32 sums). Otherwise moves h by Newton on ln N(ln h) (exponent
+// s = h N'/N measured, so steep N near clusters does not overshoot), clamped
+// to [h/8, 2h] and to hcap (L/3), bisecting the bracket when the step leaves
+// it or |f| failed to halve. *st receives kErrBoxTooSmall when the root lies
+// beyond hcap.
+__device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, double n_ngb,
+                                              double tol, double hcap, int *st) {
+  const double h = it.h;
+  const double N = (32.0 / 3.0) * (double)sw;
+  const double dN = -(32.0 / (3.0 * h)) * (double)sqdw;
+  const double f = N - n_ngb;
+  if (fabs(f) <= tol * n_ngb) return true;
+  double lo = it.lo, hi = it.hi;
+  if (f < 0.0)
+    lo = h;
+  else
+    hi = h;
+  const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
+  double hn = s_ln > 0.0 ? h * exp(log(n_ngb / N) / s_ln) : 2.0 * h;
+  hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
+  if (hi < 1e300 && (!(hn > lo && hn < hi) || fabs(f) > 0.5 * (double)it.fprev))
+    hn = 0.5 * (lo + hi);
+  it.fprev = (float)fabs(f);
+  if (hn > hcap) {
+    if (h >= hcap * (1.0 - 1e-12) && f < 0.0) *st |= kErrBoxTooSmall;
+    hn = hcap;
+  }
+  if (fabs(hn - h) <= 5e-7 * h && !(*st & kErrBoxTooSmall)) return true;
+  it.h = hn;
+  it.lo = lo;
+  it.hi = hi;
+  return false;
+}
+
+// Per-particle quantities at a converged h from the density sums `s`
+// (sum w, sum q w', sum m w, sum m (3w + q w')) and the internal energy u:
+// rho (Eq. rho), Omega = 1 + h/(3 rho) drho/dh, P = (gamma - 1) rho u, and the
+// force-stage record (h, 1/h, A (8/pi) h^-4, h^2) with A = P / (Omega rho^2).
+__device__ __forceinline__ bool finalise_density(double h, float4 s, double u, double gamma,
+                                                 float *rho_o, float *omega_o, float *P_o,
+                                                 float4 *fi_o) {
+  const double pi = 3.14159265358979323846;
+  const double h2 = h * h;
+  const double rho = 8.0 / pi * (double)s.z / (h2 * h);
+  const double drho = -8.0 / pi * (double)s.w / (h2 * h2);
+  const double omega = 1.0 + h / (3.0 * rho) * drho;
+  const double P = (gamma - 1.0) * rho * u;
+  const double A = P / (omega * rho * rho);
+  *rho_o = (float)rho;
+  *omega_o = (float)omega;
+  *P_o = (float)P;
+  const float hf = (float)h;
+  *fi_o = make_float4(hf, (float)(1.0 / h), (float)(A * 8.0 / pi / (h2 * h2)), hf * hf);
+  return rho > 0.0 && omega > 0.0 && u >= 0.0;
+}
+
+// Target group of the batched kernels: up to 32 consecutive particles (sorted
+// order) of one top cell, one warp lane each.
+struct Group {
+  int start, count;
+  int cell, box;
+  double o[3];          // frame origin: leaf-cell origin of the first particle
+                        // (relative to the top-cell origin)
+  float tlo[3], thi[3]; // bounding box, relative to the top-cell origin
+  float flo[3], fhi[3]; // bounding box in the group frame
+  float hmax;           // largest h of the group
+  int pad;
+};
+
 // ---- host-side launch wrappers (grid.cu) ----
 struct GridArgs {
   int n;                 // particles
@@ -242,6 +322,82 @@ struct ForceArgs {
   int kahan;
 };
 void launch_force(const ForceArgs &a, cudaStream_t s);
+
+// ---- batched.cu ----
+struct GroupBuildArgs {
+  int n_cells;
+  const int *cell_start, *cell_count;
+  const BoxDev *boxes;
+  int n_boxes;
+  int *gcount;           // [n_cells + 1] groups per cell (scanned in place to offsets)
+  Group *groups;
+  int n_groups;
+  const Leaf *leaves;
+  const int *leaf_of;
+  const float4 *pm;
+  const float *hf;
+};
+void launch_group_count(const GroupBuildArgs &a, cudaStream_t s);
+void launch_group_fill(const GroupBuildArgs &a, cudaStream_t s);
+void launch_group_geometry(const GroupBuildArgs &a, cudaStream_t s);
+void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s);
+
+struct GroupListArgs {
+  int n_groups;
+  const Group *groups;
+  const Leaf *leaves;
+  const Node *nodes;
+  const BoxDev *boxes;
+  int force;             // 0: density stage radius, 1: max(hmax_G, hmax_S)
+  float skin;            // density stage radius = min(skin * hmax_G, top-cell width)
+  int *count;            // [n_groups + 1]
+  const int *offset;
+  Task *tasks;
+  int *status;
+};
+void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
+
+struct BatchDensArgs {
+  int n_groups;
+  const Group *groups;
+  const int *off;
+  const Task *tasks;
+  const Leaf *leaves;
+  const int *leaf_of;
+  const float4 *pm;
+  const BoxDev *boxes;
+  double *h;
+  float *hf;
+  const float4 *vu;      // u in .w for P
+  double n_ngb, tol, gamma;
+  int max_iter;
+  float skin_stage;      // stage radius factor (matches the list build)
+  float skin_list;       // per-lane list radius factor
+  int kahan;             // compensated sums
+  unsigned char *done;
+  int *niter, *nngb;
+  float *rho, *omega, *P;
+  float4 *fi;
+  DevCounters *ctr;
+};
+void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
+
+struct BatchForceArgs {
+  int n_groups;
+  const Group *groups;
+  const int *off;
+  const Task *tasks;
+  const Leaf *leaves;
+  const int *leaf_of;
+  const float4 *pm;
+  const float4 *fi;
+  const float4 *vu;
+  float4 *acc;
+  int *nforce;
+  unsigned char *fdone;  // per particle: force written by the batched kernel
+  DevCounters *ctr;
+};
+void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 
 // ---- integrate.cu ----
 struct StoreArrays {
