@@ -370,6 +370,7 @@ def run_ours(args, d: Dist):
                        "parallelism": "replicas" if d.world > 1 else "single GPU",
                        "interactions_per_step": inter / args.steps,
                        "density_passes_last_step": s1["density_passes"],
+                       "batched_fallbacks_last_step": s1["batched_fallbacks"],
                        "leaves": s1["n_leaves"]},
             "roofline": roof,
             "stage_ms_per_step": stages,

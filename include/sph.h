@@ -103,7 +103,7 @@ typedef struct {
   int32_t density_passes;     /* density passes of the last sph_density */
   int32_t rebuilds;           /* grid / list rebuilds in the last sph_density */
   int32_t max_iter_used;      /* most passes any particle needed */
-  int32_t reserved;
+  int32_t batched_fallbacks;  /* particles the batched kernels left to the per-pass form */
   double h_min, h_max;        /* extremes of the converged h */
   /* Cumulative since sph_create (never reset): */
   int64_t total_density_interactions; /* converged-pass density interactions */

@@ -29,9 +29,9 @@ namespace sph {
 namespace {
 
 constexpr int kGroup = 32;
-constexpr int kBW = 2;          // warps per block
-constexpr int kStageD = 1024;   // density stage capacity (particles)
-constexpr int kStageF = 512;    // force stage capacity
+constexpr int kBW = 1;          // warps per block (shared memory bounds occupancy)
+constexpr int kStageD = 1536;   // density stage capacity (particles)
+constexpr int kStageF = 1024;   // force stage capacity
 constexpr int kListMax = 128;   // per-lane list capacity
 constexpr int kWalkStack = 96;
 
@@ -74,40 +74,91 @@ __device__ __forceinline__ void add_comp(float &s, float &c, float v) {
 
 // ------------------------------------------------------------- groups
 
+// Groups owned by node `id`: a top cell that is itself a leaf is cut into
+// equal chunks of <= 32; an internal node packs runs of consecutive leaf
+// children (siblings, hence spatially adjacent and contiguous in memory) into
+// groups of <= 32 and cuts any larger leaf child into equal chunks. Other
+// leaves belong to their parent's packing. `emit(start, count)` is called per
+// group; returns the number of groups.
+template <class Emit>
+__device__ int pack_node(const Node *nodes, int id, Emit emit) {
+  const Node &nd = nodes[id];
+  int ng = 0;
+  auto chunk = [&](int start, int count) {
+    const int parts = (count + kGroup - 1) / kGroup;
+    const int base = count / parts, rem = count % parts;
+    for (int p = 0; p < parts; ++p) {
+      const int sz = base + (p < rem ? 1 : 0);
+      emit(start, sz);
+      start += sz;
+      ++ng;
+    }
+  };
+  if (nd.child < 0) {
+    if (nd.parent < 0 && nd.count > 0) chunk(nd.start, nd.count);
+    return ng;
+  }
+  int run_start = 0, run_count = 0;
+  for (int o = 0; o < 8; ++o) {
+    const Node &ch = nodes[nd.child + o];
+    if (ch.count == 0) continue;
+    const bool big = ch.child >= 0 || ch.count > kGroup;
+    if (big || run_count + ch.count > kGroup) {
+      if (run_count > 0) {
+        emit(run_start, run_count);
+        ++ng;
+      }
+      run_count = 0;
+    }
+    if (ch.child >= 0) continue;  // an internal child packs its own leaves
+    if (ch.count > kGroup) {
+      chunk(ch.start, ch.count);
+      continue;
+    }
+    if (run_count == 0) run_start = ch.start;
+    run_count += ch.count;
+  }
+  if (run_count > 0) {
+    emit(run_start, run_count);
+    ++ng;
+  }
+  return ng;
+}
+
 __global__ void k_group_count(GroupBuildArgs a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < a.n_cells) a.gcount[c] = (a.cell_count[c] + kGroup - 1) / kGroup;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id < a.n_nodes) a.gcount[id] = pack_node(a.nodes, id, [](int, int) {});
 }
 
 void launch_group_count(const GroupBuildArgs &a, cudaStream_t s) {
-  k_group_count<<<(a.n_cells + 255) / 256, 256, 0, s>>>(a);
+  k_group_count<<<(a.n_nodes + 255) / 256, 256, 0, s>>>(a);
   note_launch();
 }
 
 // gcount holds the exclusive offsets here.
 __global__ void k_group_fill(GroupBuildArgs a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.n_cells) return;
-  const int cnt = a.cell_count[c], first = a.gcount[c];
-  const int box = box_of_cell_b(a.boxes, a.n_boxes, c);
-  for (int k = 0; k * kGroup < cnt; ++k) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= a.n_nodes) return;
+  const Node &nd = a.nodes[id];
+  int k = a.gcount[id];
+  pack_node(a.nodes, id, [&](int start, int count) {
     Group G;
-    G.start = a.cell_start[c] + k * kGroup;
-    G.count = min(kGroup, cnt - k * kGroup);
-    G.cell = c;
-    G.box = box;
+    G.start = start;
+    G.count = count;
+    G.cell = nd.cell;
+    G.box = nd.box;
     for (int d = 0; d < 3; ++d) {
       G.o[d] = 0.0;
       G.tlo[d] = G.thi[d] = G.flo[d] = G.fhi[d] = 0.f;
     }
     G.hmax = 0.f;
     G.pad = 0;
-    a.groups[first + k] = G;
-  }
+    a.groups[k++] = G;
+  });
 }
 
 void launch_group_fill(const GroupBuildArgs &a, cudaStream_t s) {
-  k_group_fill<<<(a.n_cells + 255) / 256, 256, 0, s>>>(a);
+  k_group_fill<<<(a.n_nodes + 255) / 256, 256, 0, s>>>(a);
   note_launch();
 }
 
@@ -422,7 +473,10 @@ __global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
   if (lane == 0) {
     if (cand) atomicAdd(&a.ctr->dens_cand, cand);
     if (inter) atomicAdd(&a.ctr->dens_inter, inter);
-    if (fallback) atomicAdd(&a.ctr->unconverged, fallback);
+    if (fallback) {
+      atomicAdd(&a.ctr->unconverged, fallback);
+      atomicAdd(&a.ctr->fallback, fallback);
+    }
     if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
     if (st_bits) atomicOr(&a.ctr->status, st_bits);
   }
@@ -443,12 +497,12 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
 
 __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
   __shared__ float4 sq_all[kBW][kStageF];   // position in the group frame, m
-  __shared__ float4 sf_all[kBW][kStageF];   // h, 1/h, A (8/pi) h^-4, global index
+  __shared__ int2 sf_all[kBW][kStageF];     // global index, h_j (bits)
   __shared__ unsigned short list_all[kBW][kListMax * 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ltmask = (1u << lane) - 1u;
   float4 *sq = sq_all[warp];
-  float4 *sf = sf_all[warp];
+  int2 *sf = sf_all[warp];
   unsigned short *list = list_all[warp];
   unsigned long long cand = 0, inter = 0;
   int fallback = 0;
@@ -497,7 +551,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
         const int pos = nst + __popc(m & ltmask);
         if (in && pos < kStageF) {
           sq[pos] = q;
-          sf[pos] = make_float4(f.x, f.y, f.z, __int_as_float(j));
+          sf[pos] = make_int2(j, __float_as_int(f.x));
         }
         nst += __popc(m);
       }
@@ -508,7 +562,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
     if (!failed) {
       for (int k = 0; k < nst; ++k) {
         const float4 q = sq[k];
-        const float hj = sf[k].x;
+        const float hj = __int_as_float(sf[k].y);
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (has && r2 > 0.f && r2 < fmaxf(hi2, hj * hj)) {
@@ -530,7 +584,8 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
       if (t < cnt) {
         const int k = list[t * 32 + lane];
         const float4 q = sq[k];
-        const float4 f = sf[k];
+        const int j = sf[k].x;
+        const float4 f = a.fi[j];
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rinv = rsqrtf(r2);
@@ -538,7 +593,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
         const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
         const float tj = f.z * dw_only(r * f.y);    // A_j dW/dr(r, h_j)
         const float fac = q.w * (ti + tj) * rinv;
-        const float4 vj = a.vu[__float_as_int(f.w)];
+        const float4 vj = a.vu[j];
         const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
         ax = fmaf(-fac, dx, ax);
         ay = fmaf(-fac, dy, ay);
@@ -560,7 +615,10 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
   if (lane == 0) {
     if (cand) atomicAdd(&a.ctr->force_cand, cand);
     if (inter) atomicAdd(&a.ctr->force_inter, inter);
-    if (fallback) atomicAdd(&a.ctr->unconverged, fallback);
+    if (fallback) {
+      atomicAdd(&a.ctr->unconverged, fallback);
+      atomicAdd(&a.ctr->fallback, fallback);
+    }
   }
 }
 

@@ -574,6 +574,8 @@ int check_status(sph_ctx *c, int st) {
 
 GroupBuildArgs group_args(sph_ctx *c) {
   GroupBuildArgs ga{};
+  ga.n_nodes = c->n_nodes;
+  ga.nodes = as<Node>(c->nodes);
   ga.n_cells = c->n_cells;
   ga.cell_start = as<int>(c->cell_start);
   ga.cell_count = as<int>(c->cell_count);
@@ -591,8 +593,9 @@ GroupBuildArgs group_args(sph_ctx *c) {
 
 // Target groups of the batched form: <= 32 consecutive particles per top cell.
 int build_groups(sph_ctx *c) {
-  const int C = c->n_cells;
+  const int C = c->n_nodes;
   TRY(ensure(c, c->gcount, sizeof(int) * (size_t)(C + 1)));
+  TRY(ensure(c, c->scan_tmp, scan_tmp_bytes(std::max(C + 1, c->n + 1))));
   CUDA_TRY(cudaMemsetAsync(as<int>(c->gcount) + C, 0, sizeof(int), c->stream));
   GroupBuildArgs ga = group_args(c);
   launch_group_count(ga, c->stream);
@@ -1065,6 +1068,7 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->density_passes = c->last_passes;
   out->rebuilds = c->last_rebuilds;
   out->max_iter_used = c->ctr_h->max_iter_used;
+  out->batched_fallbacks = c->ctr_h->fallback;
   out->total_density_interactions = (int64_t)c->total_dens_inter;
   out->total_force_interactions = (int64_t)c->total_force_inter;
   out->density_launches = c->dens_launches;

@@ -82,7 +82,8 @@ struct DevCounters {
   int max_iter_used;
   int n_active;
   int n_frontier;
-  int pad[3];
+  int fallback;                       // particles the batched kernels left to the per-pass form
+  int pad[2];
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
@@ -325,11 +326,13 @@ void launch_force(const ForceArgs &a, cudaStream_t s);
 
 // ---- batched.cu ----
 struct GroupBuildArgs {
+  int n_nodes;
+  const Node *nodes;
   int n_cells;
   const int *cell_start, *cell_count;
   const BoxDev *boxes;
   int n_boxes;
-  int *gcount;           // [n_cells + 1] groups per cell (scanned in place to offsets)
+  int *gcount;           // [n_nodes + 1] groups per node (scanned in place to offsets)
   Group *groups;
   int n_groups;
   const Leaf *leaves;

@@ -56,7 +56,7 @@ class sph_stats_t(ctypes.Structure):
                 ("density_pair_candidates", ctypes.c_int64),
                 ("force_pair_candidates", ctypes.c_int64),
                 ("density_passes", ctypes.c_int32), ("rebuilds", ctypes.c_int32),
-                ("max_iter_used", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_iter_used", ctypes.c_int32), ("batched_fallbacks", ctypes.c_int32),
                 ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
                 ("total_density_interactions", ctypes.c_int64),
                 ("total_force_interactions", ctypes.c_int64),
