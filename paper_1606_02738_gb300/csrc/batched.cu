@@ -29,10 +29,6 @@ namespace sph {
 namespace {
 
 constexpr int kGroup = 32;
-constexpr int kBW = 1;          // warps per block (shared memory bounds occupancy)
-constexpr int kStageD = 1536;   // density stage capacity (particles)
-constexpr int kStageF = 1024;   // force stage capacity
-constexpr int kListMax = 128;   // per-lane list capacity
 constexpr int kWalkStack = 96;
 
 __device__ __forceinline__ int box_of_cell_b(const BoxDev *b, int nb, int c) {
@@ -293,20 +289,100 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
   note_launch();
 }
 
-// ------------------------------------------------------------ density
+// ------------------------------------------------------------ kernels
+//
+// One block of kNW warps per group. Warp w stages the tasks e0 + w, e0 + w +
+// kNW, ... into its own segment of the stage and keeps, per lane (= target
+// particle), a list of the entries of that segment within the lane's radius.
+// Partial sums of the warps are added in fixed warp order through shared
+// memory, so every warp holds identical totals and runs the identical h
+// update: no broadcast, and results do not depend on timing.
+
+constexpr int kNW = 4;           // warps per block, one group per block
+constexpr int kSegD = 384;       // density stage entries per warp
+constexpr int kListD = 64;       // density list entries per lane per warp
+constexpr int kSegF = 256;       // force stage entries per warp
+constexpr int kListF = 48;       // force list entries per lane per warp
+
+struct DensSmem {
+  float4 stage[kNW][kSegD];                 // position in the group frame, m
+  unsigned short list[kNW][kListD * 32];    // [entry][lane]
+  float4 red[kNW][32];                      // per-warp partial sums
+  int redc[kNW][32];                        // per-warp partial counts
+};
+
+struct ForceSmem {
+  float4 sq[kNW][kSegF];                    // position in the group frame, m
+  float4 sf[kNW][kSegF];                    // h, 1/h, A (8/pi) h^-4, h^2
+  float4 sv[kNW][kSegF];                    // v, u
+  unsigned short list[kNW][kListF * 32];
+  float4 red[kNW][32];
+};
+
+// Stage, into this warp's segment, the particles of its share of the group's
+// source leaves that lie within `R` (per candidate: R = Rg, or max(Rg, h_j)
+// for the force) of the group box. Returns the number of entries (more than
+// `cap` means overflow).
+template <bool FORCE>
+__device__ int stage_group(const BatchDensArgs *da, const BatchForceArgs *fa, const Group &G,
+                           int e0, int e1, int warp, int lane, float Rg, float4 *sq, float4 *sf,
+                           float4 *sv, int cap) {
+  const unsigned ltmask = (1u << lane) - 1u;
+  const Task *tasks = FORCE ? fa->tasks : da->tasks;
+  const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
+  const float4 *pm = FORCE ? fa->pm : da->pm;
+  int nst = 0;
+  for (int e = e0 + warp; e < e1; e += kNW) {
+    const Task tk = tasks[e];
+    const Leaf &LS = leaves[tk.src];
+    const int js = LS.start, jn = LS.count;
+    for (int jb = 0; jb < jn; jb += 32) {
+      bool in = false;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q, v = q;
+      const int j = js + jb + lane;
+      if (jb + lane < jn) {
+        q = pm[j];
+        q.x += tk.sx;
+        q.y += tk.sy;
+        q.z += tk.sz;
+        float R = Rg;
+        if (FORCE) {
+          f = fa->fi[j];
+          v = fa->vu[j];
+          R = fmaxf(Rg, f.x);
+        }
+        const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
+        const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
+        const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
+        in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      const int pos = nst + __popc(m & ltmask);
+      if (in && pos < cap) {
+        sq[pos] = q;
+        if (FORCE) {
+          sf[pos] = f;
+          sv[pos] = v;
+        }
+      }
+      nst += __popc(m);
+    }
+  }
+  __syncwarp();
+  return nst;
+}
 
 template <bool KAHAN>
-__global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
-  __shared__ float4 stage_all[kBW][kStageD];
-  __shared__ unsigned short list_all[kBW][kListMax * 32];
+__global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DensSmem &S = *reinterpret_cast<DensSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned ltmask = (1u << lane) - 1u;
-  float4 *stage = stage_all[warp];
-  unsigned short *list = list_all[warp];
+  float4 *stage = S.stage[warp];
+  unsigned short *list = S.list[warp];
   unsigned long long cand = 0, inter = 0;
   int fallback = 0, max_it = 0, st_bits = 0;
 
-  for (int g = blockIdx.x * kBW + warp; g < a.n_groups; g += gridDim.x * kBW) {
+  for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
@@ -328,46 +404,18 @@ __global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
       it.h = a.h[i];
     }
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
-    const float Rg2 = Rg * Rg;
+    const int nst = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane, Rg,
+                                       stage, nullptr, nullptr, kSegD);
+    bool failed = __syncthreads_or(nst > kSegD) != 0;
 
-    // stage the candidates within Rg of the group box
-    int nst = 0;
-    const int e0 = a.off[g], e1 = a.off[g + 1];
-    for (int e = e0; e < e1; ++e) {
-      const Task tk = a.tasks[e];
-      const Leaf &LS = a.leaves[tk.src];
-      const int js = LS.start, jn = LS.count;
-      for (int jb = 0; jb < jn; jb += 32) {
-        bool in = false;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jb + lane < jn) {
-          q = a.pm[js + jb + lane];
-          q.x += tk.sx;
-          q.y += tk.sy;
-          q.z += tk.sz;
-          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
-          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
-          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
-          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < Rg2;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        const int pos = nst + __popc(m & ltmask);
-        if (in && pos < kStageD) stage[pos] = q;
-        nst += __popc(m);
-      }
-    }
-    __syncwarp();
-    bool failed = nst > kStageD;
-
-    bool fin = !has;
-    bool need = has;
+    bool fin = !has, need = has;
     int cnt = 0, passes = 0, ngb = 0;
     float rl = 0.f;
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; !failed && pass < a.max_iter; ++pass) {
-      // (re)build the lists of lanes whose h outgrew their list radius
+      // (re)build this warp's lists for lanes whose h outgrew the list radius
       const bool bld = need && !fin;
-      if (__any_sync(0xffffffffu, bld)) {
+      if (__syncthreads_or(bld)) {
         float rl2 = -1.f;
         if (bld) {
           rl = fminf((float)it.h * a.skin_list, Rg);
@@ -380,18 +428,17 @@ __global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (r2 < rl2) {
-            if (cnt < kListMax) list[cnt * 32 + lane] = (unsigned short)k;
+            if (cnt < kListD) list[cnt * 32 + lane] = (unsigned short)k;
             ++cnt;
           }
         }
         need = false;
-        if (__any_sync(0xffffffffu, cnt > kListMax)) {
+        if (__syncthreads_or(cnt > kListD)) {
           failed = true;
           break;
         }
-        __syncwarp();
       }
-      // sums at the current h
+      // partial sums of this warp at the current h
       const float hf = (float)it.h;
       const float h2 = fin ? -1.f : hf * hf;
       const float hinv = 1.f / hf;
@@ -425,29 +472,43 @@ __global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
           }
         }
       }
+      if (!fin) cand += cnt;
+      S.red[warp][lane] = make_float4(sw, sdw, smw, smdh);
+      S.redc[warp][lane] = c;
+      __syncthreads();
+      float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+      int ctot = 0;
+      for (int w = 0; w < kNW; ++w) {  // fixed order: identical totals in every warp
+        const float4 r = S.red[w][lane];
+        tot.x += r.x;
+        tot.y += r.y;
+        tot.z += r.z;
+        tot.w += r.w;
+        ctot += S.redc[w][lane];
+      }
+      __syncthreads();
       if (!fin) {
-        cand += cnt;
         ++passes;
         int st = 0;
-        const bool conv = h_newton_step(it, sw, sdw, a.n_ngb, a.tol, hcap, &st);
+        const bool conv = h_newton_step(it, tot.x, tot.y, a.n_ngb, a.tol, hcap, &st);
         st_bits |= st;
         if (conv) {
           fin = true;
-          fs = make_float4(sw, sdw, smw, smdh);
-          ngb = c - 1;  // the self term is always inside
+          fs = tot;
+          ngb = ctot - 1;  // the self term is always inside
         } else if ((float)it.h > rl) {
           need = true;
         }
       }
-      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rg)) failed = true;  // beyond the stage
-      if (__all_sync(0xffffffffu, fin)) break;
+      if (__syncthreads_or(!fin && (float)it.h > Rg)) failed = true;  // beyond the stage
+      if (__syncthreads_and(fin)) break;
     }
-    if (failed || !__all_sync(0xffffffffu, fin)) {
-      // left to the per-pass form: keep the incoming h and flags
-      if (has) ++fallback;
+    const bool all_fin = __syncthreads_and(fin) != 0;
+    if (failed || !all_fin) {
+      if (warp == 0 && has) ++fallback;  // left to the per-pass form
       continue;
     }
-    if (has) {
+    if (warp == 0 && has) {
       float rho, omega, P;
       float4 fi;
       const bool ok = finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi);
@@ -484,30 +545,36 @@ __global__ void __launch_bounds__(kBW * 32) k_density_batched(BatchDensArgs a) {
 
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  int blocks = (a.n_groups + kBW - 1) / kBW;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  static bool attr = false;
+  const int bytes = (int)sizeof(DensSmem);
+  if (!attr) {
+    cudaFuncSetAttribute(k_density_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    cudaFuncSetAttribute(k_density_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    attr = true;
+  }
+  int blocks = a.n_groups;
+  if (blocks > 152 * 64) blocks = 152 * 64;
   if (a.kahan)
-    k_density_batched<true><<<blocks, kBW * 32, 0, s>>>(a);
+    k_density_batched<true><<<blocks, kNW * 32, bytes, s>>>(a);
   else
-    k_density_batched<false><<<blocks, kBW * 32, 0, s>>>(a);
+    k_density_batched<false><<<blocks, kNW * 32, bytes, s>>>(a);
   note_launch();
 }
 
-// -------------------------------------------------------------- force
-
-__global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
-  __shared__ float4 sq_all[kBW][kStageF];   // position in the group frame, m
-  __shared__ int2 sf_all[kBW][kStageF];     // global index, h_j (bits)
-  __shared__ unsigned short list_all[kBW][kListMax * 32];
+__global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned ltmask = (1u << lane) - 1u;
-  float4 *sq = sq_all[warp];
-  int2 *sf = sf_all[warp];
-  unsigned short *list = list_all[warp];
+  float4 *sq = S.sq[warp];
+  float4 *sf = S.sf[warp];
+  float4 *sv = S.sv[warp];
+  unsigned short *list = S.list[warp];
   unsigned long long cand = 0, inter = 0;
   int fallback = 0;
 
-  for (int g = blockIdx.x * kBW + warp; g < a.n_groups; g += gridDim.x * kBW) {
+  for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
     const bool has = lane < G.count;
     const int i = G.start + lane;
@@ -522,60 +589,27 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
       fi = a.fi[i];
       vi = a.vu[i];
     }
-    const float hi2 = has ? fi.x * fi.x : -1.f;
-
-    // stage: j within max(hmax_G, h_j) of the group box
-    int nst = 0;
-    const int e0 = a.off[g], e1 = a.off[g + 1];
-    for (int e = e0; e < e1; ++e) {
-      const Task tk = a.tasks[e];
-      const Leaf &LS = a.leaves[tk.src];
-      const int js = LS.start, jn = LS.count;
-      for (int jb = 0; jb < jn; jb += 32) {
-        bool in = false;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q;
-        const int j = js + jb + lane;
-        if (jb + lane < jn) {
-          q = a.pm[j];
-          f = a.fi[j];
-          q.x += tk.sx;
-          q.y += tk.sy;
-          q.z += tk.sz;
-          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
-          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
-          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
-          const float R = fmaxf(G.hmax, f.x);
-          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        const int pos = nst + __popc(m & ltmask);
-        if (in && pos < kStageF) {
-          sq[pos] = q;
-          sf[pos] = make_int2(j, __float_as_int(f.x));
-        }
-        nst += __popc(m);
-      }
-    }
-    __syncwarp();
-    bool failed = nst > kStageF;
+    const float hi2 = has ? fi.w : -1.f;
+    const int nst = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
+                                      G.hmax, sq, sf, sv, kSegF);
+    bool failed = __syncthreads_or(nst > kSegF) != 0;
     int cnt = 0;
     if (!failed) {
       for (int k = 0; k < nst; ++k) {
         const float4 q = sq[k];
-        const float hj = __int_as_float(sf[k].y);
+        const float hj2 = sf[k].w;
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj * hj)) {
-          if (cnt < kListMax) list[cnt * 32 + lane] = (unsigned short)k;
+        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+          if (cnt < kListF) list[cnt * 32 + lane] = (unsigned short)k;
           ++cnt;
         }
       }
       if (has) cand += nst;
-      failed = __any_sync(0xffffffffu, cnt > kListMax);
-      __syncwarp();
+      failed = __syncthreads_or(cnt > kListF) != 0;
     }
     if (failed) {
-      if (has) ++fallback;
+      if (warp == 0 && has) ++fallback;
       continue;
     }
     float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
@@ -584,8 +618,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
       if (t < cnt) {
         const int k = list[t * 32 + lane];
         const float4 q = sq[k];
-        const int j = sf[k].x;
-        const float4 f = a.fi[j];
+        const float4 f = sf[k];
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rinv = rsqrtf(r2);
@@ -593,7 +626,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
         const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
         const float tj = f.z * dw_only(r * f.y);    // A_j dW/dr(r, h_j)
         const float fac = q.w * (ti + tj) * rinv;
-        const float4 vj = a.vu[j];
+        const float4 vj = sv[k];
         const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
         ax = fmaf(-fac, dx, ax);
         ay = fmaf(-fac, dy, ay);
@@ -601,13 +634,39 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
         du = fmaf(q.w * ti * rinv, dvdx, du);
       }
     }
-    if (has) {
-      a.acc[i] = make_float4(ax, ay, az, du);
-      a.nforce[i] = cnt;
-      a.fdone[i] = 1;
-      inter += (unsigned long long)cnt;
-      cand += cnt;
+    S.red[warp][lane] = make_float4(ax, ay, az, du);
+    int ctot = cnt;
+    __syncthreads();
+    if (warp == 0) {
+      float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int w = 0; w < kNW; ++w) {
+        const float4 r = S.red[w][lane];
+        tot.x += r.x;
+        tot.y += r.y;
+        tot.z += r.z;
+        tot.w += r.w;
+      }
+      S.red[0][lane] = tot;  // warp 0 alone reads and writes its own row
     }
+    // counts: every warp adds its own
+    if (has) {
+      inter += (unsigned long long)ctot;
+      cand += ctot;
+    }
+    __syncthreads();
+    if (warp == 0 && has) {
+      a.acc[i] = S.red[0][lane];
+      a.fdone[i] = 1;
+    }
+    // per-particle count: sum over warps through the (now free) red rows
+    if (has) S.red[warp][lane].x = __int_as_float(ctot);
+    __syncthreads();
+    if (warp == 0 && has) {
+      int n = 0;
+      for (int w = 0; w < kNW; ++w) n += __float_as_int(S.red[w][lane].x);
+      a.nforce[i] = n;
+    }
+    __syncthreads();
   }
   cand = warp_sum(cand);
   inter = warp_sum(inter);
@@ -624,9 +683,15 @@ __global__ void __launch_bounds__(kBW * 32) k_force_batched(BatchForceArgs a) {
 
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  int blocks = (a.n_groups + kBW - 1) / kBW;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  k_force_batched<<<blocks, kBW * 32, 0, s>>>(a);
+  static bool attr = false;
+  const int bytes = (int)sizeof(ForceSmem);
+  if (!attr) {
+    cudaFuncSetAttribute(k_force_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  int blocks = a.n_groups;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  k_force_batched<<<blocks, kNW * 32, bytes, s>>>(a);
   note_launch();
 }
 
