@@ -371,6 +371,7 @@ def run_ours(args, d: Dist):
                        "interactions_per_step": inter / args.steps,
                        "density_passes_last_step": s1["density_passes"],
                        "batched_fallbacks_last_step": s1["batched_fallbacks"],
+                       "stage_max": [s1["stage_max_density"], s1["stage_max_force"]],
                        "leaves": s1["n_leaves"]},
             "roofline": roof,
             "stage_ms_per_step": stages,

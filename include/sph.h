@@ -105,6 +105,8 @@ typedef struct {
   int32_t max_iter_used;      /* most passes any particle needed */
   int32_t batched_fallbacks;  /* particles the batched kernels left to the per-pass form */
   double h_min, h_max;        /* extremes of the converged h */
+  int32_t stage_max_density;  /* largest candidate stage of a batched density group */
+  int32_t stage_max_force;    /* largest candidate stage of a batched force group */
   /* Cumulative since sph_create (never reset): */
   int64_t total_density_interactions; /* converged-pass density interactions */
   int64_t total_force_interactions;

@@ -299,77 +299,101 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
 // update: no broadcast, and results do not depend on timing.
 
 constexpr int kNW = 4;           // warps per block, one group per block
-constexpr int kSegD = 384;       // density stage entries per warp
+constexpr int kStageD = 1792;    // density stage entries per group (shared by the warps)
 constexpr int kListD = 64;       // density list entries per lane per warp
-constexpr int kSegF = 256;       // force stage entries per warp
+constexpr int kStageF = 1024;    // force stage entries per group
 constexpr int kListF = 48;       // force list entries per lane per warp
 
 struct DensSmem {
-  float4 stage[kNW][kSegD];                 // position in the group frame, m
+  float4 stage[kStageD];                    // position in the group frame, m
   unsigned short list[kNW][kListD * 32];    // [entry][lane]
   float4 red[kNW][32];                      // per-warp partial sums
   int redc[kNW][32];                        // per-warp partial counts
+  int wcount[kNW];                          // stage entries of each warp
 };
 
 struct ForceSmem {
-  float4 sq[kNW][kSegF];                    // position in the group frame, m
-  float4 sf[kNW][kSegF];                    // h, 1/h, A (8/pi) h^-4, h^2
-  float4 sv[kNW][kSegF];                    // v, u
+  float4 sq[kStageF];                       // position in the group frame, m
+  float4 sf[kStageF];                       // h, 1/h, A (8/pi) h^-4, h^2
+  float4 sv[kStageF];                       // v, u
   unsigned short list[kNW][kListF * 32];
   float4 red[kNW][32];
+  int wcount[kNW];
 };
 
-// Stage, into this warp's segment, the particles of its share of the group's
-// source leaves that lie within `R` (per candidate: R = Rg, or max(Rg, h_j)
-// for the force) of the group box. Returns the number of entries (more than
-// `cap` means overflow).
+struct StageRange {
+  int base, count, total;  // this warp's entries [base, base + count); all warps' total
+};
+
+// Stage the particles of this warp's share of the group's source leaves that
+// lie within R of the group box (R = Rg, or max(Rg, h_j) for the force). A
+// count pass sizes each warp's share, the warps' shares are laid out in warp
+// order, and a write pass fills them: block-wide capacity, deterministic order.
+// Must be called by every thread of the block. total > cap means overflow.
 template <bool FORCE>
-__device__ int stage_group(const BatchDensArgs *da, const BatchForceArgs *fa, const Group &G,
-                           int e0, int e1, int warp, int lane, float Rg, float4 *sq, float4 *sf,
-                           float4 *sv, int cap) {
+__device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
+                                  const Group &G, int e0, int e1, int warp, int lane, float Rg,
+                                  float4 *sq, float4 *sf, float4 *sv, int *wcount, int cap) {
   const unsigned ltmask = (1u << lane) - 1u;
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
   const float4 *pm = FORCE ? fa->pm : da->pm;
-  int nst = 0;
-  for (int e = e0 + warp; e < e1; e += kNW) {
-    const Task tk = tasks[e];
-    const Leaf &LS = leaves[tk.src];
-    const int js = LS.start, jn = LS.count;
-    for (int jb = 0; jb < jn; jb += 32) {
-      bool in = false;
-      float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q, v = q;
-      const int j = js + jb + lane;
-      if (jb + lane < jn) {
-        q = pm[j];
-        q.x += tk.sx;
-        q.y += tk.sy;
-        q.z += tk.sz;
-        float R = Rg;
-        if (FORCE) {
-          f = fa->fi[j];
-          v = fa->vu[j];
-          R = fmaxf(Rg, f.x);
+  StageRange r;
+  r.base = 0;
+  for (int write = 0; write < 2; ++write) {
+    int nst = 0;
+    for (int e = e0 + warp; e < e1; e += kNW) {
+      const Task tk = tasks[e];
+      const Leaf &LS = leaves[tk.src];
+      const int js = LS.start, jn = LS.count;
+      for (int jb = 0; jb < jn; jb += 32) {
+        bool in = false;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q;
+        const int j = js + jb + lane;
+        if (jb + lane < jn) {
+          q = pm[j];
+          q.x += tk.sx;
+          q.y += tk.sy;
+          q.z += tk.sz;
+          float R = Rg;
+          if (FORCE) {
+            f = fa->fi[j];
+            R = fmaxf(Rg, f.x);
+          }
+          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
+          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
+          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
+          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
         }
-        const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
-        const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
-        const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
-        in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, in);
-      const int pos = nst + __popc(m & ltmask);
-      if (in && pos < cap) {
-        sq[pos] = q;
-        if (FORCE) {
-          sf[pos] = f;
-          sv[pos] = v;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (write) {
+          const int pos = r.base + nst + __popc(m & ltmask);
+          if (in && pos < cap) {
+            sq[pos] = q;
+            if (FORCE) {
+              sf[pos] = f;
+              sv[pos] = fa->vu[j];
+            }
+          }
         }
+        nst += __popc(m);
       }
-      nst += __popc(m);
+    }
+    if (!write) {
+      if (lane == 0) wcount[warp] = nst;
+      __syncthreads();
+      r.total = 0;
+      for (int w = 0; w < kNW; ++w) {
+        if (w < warp) r.base += wcount[w];
+        r.total += wcount[w];
+      }
+      r.count = nst;
+      __syncthreads();
+      if (r.total > cap) break;  // block-uniform
     }
   }
-  __syncwarp();
-  return nst;
+  __syncthreads();
+  return r;
 }
 
 template <bool KAHAN>
@@ -377,10 +401,10 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem &S = *reinterpret_cast<DensSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *stage = S.stage[warp];
+  float4 *stage = S.stage;
   unsigned short *list = S.list[warp];
   unsigned long long cand = 0, inter = 0;
-  int fallback = 0, max_it = 0, st_bits = 0;
+  int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0;
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
@@ -404,9 +428,11 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
       it.h = a.h[i];
     }
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
-    const int nst = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane, Rg,
-                                       stage, nullptr, nullptr, kSegD);
-    bool failed = __syncthreads_or(nst > kSegD) != 0;
+    const StageRange sr = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane,
+                                             Rg, stage, nullptr, nullptr, S.wcount, kStageD);
+    stage_max = max(stage_max, sr.total);
+    bool failed = sr.total > kStageD;  // block-uniform
+    const int k0 = sr.base, k1 = sr.base + sr.count;
 
     bool fin = !has, need = has;
     int cnt = 0, passes = 0, ngb = 0;
@@ -421,9 +447,9 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
           rl = fminf((float)it.h * a.skin_list, Rg);
           rl2 = rl * rl;
           cnt = 0;
-          cand += nst;
+          cand += sr.count;
         }
-        for (int k = 0; k < nst; ++k) {
+        for (int k = k0; k < k1; ++k) {
           const float4 q = stage[k];
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -540,6 +566,7 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
     }
     if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
     if (st_bits) atomicOr(&a.ctr->status, st_bits);
+    atomicMax(&a.ctr->stage_max[0], stage_max);
   }
 }
 
@@ -567,12 +594,12 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *sq = S.sq[warp];
-  float4 *sf = S.sf[warp];
-  float4 *sv = S.sv[warp];
+  float4 *sq = S.sq;
+  float4 *sf = S.sf;
+  float4 *sv = S.sv;
   unsigned short *list = S.list[warp];
   unsigned long long cand = 0, inter = 0;
-  int fallback = 0;
+  int fallback = 0, stage_max = 0;
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
@@ -590,12 +617,13 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
       vi = a.vu[i];
     }
     const float hi2 = has ? fi.w : -1.f;
-    const int nst = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
-                                      G.hmax, sq, sf, sv, kSegF);
-    bool failed = __syncthreads_or(nst > kSegF) != 0;
+    const StageRange sr = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
+                                            G.hmax, sq, sf, sv, S.wcount, kStageF);
+    stage_max = max(stage_max, sr.total);
+    bool failed = sr.total > kStageF;  // block-uniform
     int cnt = 0;
     if (!failed) {
-      for (int k = 0; k < nst; ++k) {
+      for (int k = sr.base; k < sr.base + sr.count; ++k) {
         const float4 q = sq[k];
         const float hj2 = sf[k].w;
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
@@ -605,7 +633,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
           ++cnt;
         }
       }
-      if (has) cand += nst;
+      if (has) cand += sr.count;
       failed = __syncthreads_or(cnt > kListF) != 0;
     }
     if (failed) {
@@ -678,6 +706,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
       atomicAdd(&a.ctr->unconverged, fallback);
       atomicAdd(&a.ctr->fallback, fallback);
     }
+    atomicMax(&a.ctr->stage_max[1], stage_max);
   }
 }
 

@@ -215,10 +215,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(ForceArgs a) {
   __shared__ float4 sv[kWarpsPerBlock][kStage];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long cand = 0, inter = 0;
-  for (int T = blockIdx.x * kWarpsPerBlock + warp; T < a.n_leaves;
-       T += gridDim.x * kWarpsPerBlock) {
+  for (int t = blockIdx.x * kWarpsPerBlock + warp; t < a.n_targets;
+       t += gridDim.x * kWarpsPerBlock) {
+    const int T = a.active ? a.active[t] : t;
     const Leaf LT = a.leaves[T];
-    const int e0 = a.list_off[T], e1 = a.list_off[T + 1];
+    const int e0 = a.list_off[t], e1 = a.list_off[t + 1];
     for (int ib = 0; ib < LT.count; ib += 32) {
       const int i = LT.start + ib + lane;
       const bool has = ib + lane < LT.count;
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(ForceArgs a) {
           if (has) cand += nj;
         }
       }
-      if (has) {
+      if (has && !(a.skip && a.skip[i])) {
         a.acc[i] = make_float4(ax, ay, az, du);
         a.nforce[i] = c;
         inter += c;
@@ -297,8 +298,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(ForceArgs a) {
 }
 
 void launch_force(const ForceArgs &a, cudaStream_t s) {
-  if (a.n_leaves <= 0) return;
-  int blocks = (a.n_leaves + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (a.n_targets <= 0) return;
+  int blocks = (a.n_targets + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (a.kahan)
     k_force<true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(a);

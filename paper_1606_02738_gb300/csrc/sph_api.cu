@@ -809,6 +809,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
   fa.groups = as<Group>(c->groups);
@@ -830,31 +831,40 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   c->force_pending = true;
   TRY(read_counters(c));
   *all_done = c->ctr_h->unconverged == 0;
-  if (*all_done)
-    c->force_valid = true;
-  else
-    c->total_force_inter -= c->ctr_h->force_inter;  // the per-leaf pass recounts all
+  if (*all_done) c->force_valid = true;
   return sync_check(c);
 }
 
 int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
   if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
+  const int *active = nullptr;
+  int n_targets = c->n_leaves;
+  const unsigned char *skip = nullptr;
   if (c->p.mode == SPH_MODE_BATCHED && c->p.precision == SPH_PREC_FP32) {
     bool all = false;
     TRY(force_batched(c, vu_for_force, &all));
     if (all) return SPH_OK;
-    // some group overflowed its stage: the per-leaf form recomputes every particle
+    // groups that overflowed their stage: the per-leaf form finishes the
+    // leaves holding their particles, skipping particles already done
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->n_active, 0, sizeof(int), c->stream));
+    launch_active_leaves(as<Leaf>(c->leaves), c->n_leaves, c->fdone, as<int>(c->active), c->ctr,
+                         c->stream);
     TRY(read_counters(c));
+    active = as<int>(c->active);
+    n_targets = c->ctr_h->n_active;
+    skip = c->fdone;
   }
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
-  TRY(build_lists(c, true, nullptr, c->n_leaves, c->force_off, c->force_tasks,
-                  c->n_force_tasks));
+  TRY(build_lists(c, true, active, n_targets, c->force_off, c->force_tasks, c->n_force_tasks));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
   ForceArgs fa{};
   fa.n_leaves = c->n_leaves;
+  fa.active = active;
+  fa.n_targets = n_targets;
+  fa.skip = skip;
   fa.leaves = as<Leaf>(c->leaves);
   fa.list_off = as<int>(c->force_off);
   fa.tasks = as<Task>(c->force_tasks);
@@ -1069,6 +1079,8 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->rebuilds = c->last_rebuilds;
   out->max_iter_used = c->ctr_h->max_iter_used;
   out->batched_fallbacks = c->ctr_h->fallback;
+  out->stage_max_density = c->ctr_h->stage_max[0];
+  out->stage_max_force = c->ctr_h->stage_max[1];
   out->total_density_interactions = (int64_t)c->total_dens_inter;
   out->total_force_interactions = (int64_t)c->total_force_inter;
   out->density_launches = c->dens_launches;

@@ -83,7 +83,7 @@ struct DevCounters {
   int n_active;
   int n_frontier;
   int fallback;                       // particles the batched kernels left to the per-pass form
-  int pad[2];
+  int stage_max[2];                   // largest group stage (density, force) of the batched form
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
@@ -310,7 +310,10 @@ void launch_active_leaves(const Leaf *leaves, int n_leaves, const unsigned char 
                           int *active, DevCounters *ctr, cudaStream_t s);
 
 struct ForceArgs {
-  int n_leaves;
+  int n_leaves;                // targets: n_targets leaves, active[t] (or t when null)
+  const int *active;
+  int n_targets;
+  const unsigned char *skip;   // optional: particles already finished (not written)
   const Leaf *leaves;
   const int *list_off;
   const Task *tasks;

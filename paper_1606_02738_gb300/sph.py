@@ -58,6 +58,7 @@ class sph_stats_t(ctypes.Structure):
                 ("density_passes", ctypes.c_int32), ("rebuilds", ctypes.c_int32),
                 ("max_iter_used", ctypes.c_int32), ("batched_fallbacks", ctypes.c_int32),
                 ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("stage_max_density", ctypes.c_int32), ("stage_max_force", ctypes.c_int32),
                 ("total_density_interactions", ctypes.c_int64),
                 ("total_force_interactions", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("density_launches", ctypes.c_int64),

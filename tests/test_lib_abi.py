@@ -46,7 +46,7 @@ def test_params_struct_matches_header_defaults(libpath):
     assert p.n_ngb == 48.0 and p.h_tol == 1e-6 and p.max_iter == 30 and p.n_split == 64
     assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4
     assert [f for f, _ in sph.sph_params._fields_][-2:] == ["profile", "reserved"]
-    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 5 * 8 + 6 * 8
+    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 6 * 8
 
 
 def test_invalid_arguments_rejected_without_gpu(libpath):
