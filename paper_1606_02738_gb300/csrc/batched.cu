@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
                                              Rg, stage, nullptr, nullptr, S.wcount, kStageD);
     stage_max = max(stage_max, sr.total);
     bool failed = sr.total > kStageD;  // block-uniform
-    const int k0 = sr.base, k1 = sr.base + sr.count;
+    const int nst = min(sr.total, kStageD);
 
     bool fin = !has, need = has;
     int cnt = 0, passes = 0, ngb = 0;
@@ -447,9 +447,9 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
           rl = fminf((float)it.h * a.skin_list, Rg);
           rl2 = rl * rl;
           cnt = 0;
-          cand += sr.count;
+          cand += (nst + kNW - 1 - warp) / kNW;
         }
-        for (int k = k0; k < k1; ++k) {
+        for (int k = warp; k < nst; k += kNW) {  // interleaved: balanced lists
           const float4 q = stage[k];
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
     bool failed = sr.total > kStageF;  // block-uniform
     int cnt = 0;
     if (!failed) {
-      for (int k = sr.base; k < sr.base + sr.count; ++k) {
+      for (int k = warp; k < sr.total; k += kNW) {  // interleaved: balanced lists
         const float4 q = sq[k];
         const float hj2 = sf[k].w;
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
           ++cnt;
         }
       }
-      if (has) cand += sr.count;
+      if (has) cand += (sr.total + kNW - 1 - warp) / kNW;
       failed = __syncthreads_or(cnt > kListF) != 0;
     }
     if (failed) {

@@ -828,8 +828,8 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
   ++c->force_launches;
-  c->force_pending = true;
   TRY(read_counters(c));
+  c->force_pending = true;  // banked by the next read, with any per-leaf remainder
   *all_done = c->ctr_h->unconverged == 0;
   if (*all_done) c->force_valid = true;
   return sync_check(c);
@@ -851,6 +851,9 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
     launch_active_leaves(as<Leaf>(c->leaves), c->n_leaves, c->fdone, as<int>(c->active), c->ctr,
                          c->stream);
     TRY(read_counters(c));
+    // that read banked the batched counts; they are banked again, with the
+    // remainder's, after the per-leaf pass
+    c->total_force_inter -= c->ctr_h->force_inter;
     active = as<int>(c->active);
     n_targets = c->ctr_h->n_active;
     skip = c->fdone;
@@ -858,8 +861,10 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
   TRY(build_lists(c, true, active, n_targets, c->force_off, c->force_tasks, c->n_force_tasks));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+  if (!skip) {  // a remainder after the batched pass keeps adding to its counters
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+  }
   ForceArgs fa{};
   fa.n_leaves = c->n_leaves;
   fa.active = active;
