@@ -291,33 +291,35 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
 
 // ------------------------------------------------------------ kernels
 //
-// One block of kNW warps per group. Warp w stages the tasks e0 + w, e0 + w +
-// kNW, ... into its own segment of the stage and keeps, per lane (= target
-// particle), a list of the entries of that segment within the lane's radius.
-// Partial sums of the warps are added in fixed warp order through shared
-// memory, so every warp holds identical totals and runs the identical h
-// update: no broadcast, and results do not depend on timing.
+// One block of kNW warps per group. All warps stage the group's candidates
+// together (a count pass, then per-warp shares laid out in warp order: the
+// stage order never depends on timing). Then each warp works alone on a
+// sub-cluster of 8 consecutive targets (compact: consecutive in octree
+// order): it keeps the staged entries within its sub-cluster's radius, and
+// gives every target 4 lanes, lane s of a target handling every 4th of those
+// entries; the 4 partial sums are combined by shuffles in fixed order, so the
+// 4 lanes hold identical totals and take identical h steps.
 
 constexpr int kNW = 4;           // warps per block, one group per block
-constexpr int kStageD = 1792;    // density stage entries per group (shared by the warps)
-constexpr int kListD = 64;       // density list entries per lane per warp
-constexpr int kStageF = 1024;    // force stage entries per group
-constexpr int kListF = 48;       // force list entries per lane per warp
+constexpr int kSub = 8;          // targets per warp
+constexpr int kSlice = 4;        // lanes per target
+constexpr int kStageD = 1536;    // density stage entries per group
+constexpr int kStageF = 896;     // force stage entries per group
+constexpr int kLane = 32;        // list entries per lane
 
 struct DensSmem {
   float4 stage[kStageD];                    // position in the group frame, m
-  unsigned short list[kNW][kListD * 32];    // [entry][lane]
-  float4 red[kNW][32];                      // per-warp partial sums
-  int redc[kNW][32];                        // per-warp partial counts
-  int wcount[kNW];                          // stage entries of each warp
+  unsigned short cand[kNW][kStageD];        // each warp's pre-filtered entries
+  unsigned short list[kNW][kLane * 32];     // [entry][lane]
+  int wcount[kNW];
 };
 
 struct ForceSmem {
   float4 sq[kStageF];                       // position in the group frame, m
   float4 sf[kStageF];                       // h, 1/h, A (8/pi) h^-4, h^2
   float4 sv[kStageF];                       // v, u
-  unsigned short list[kNW][kListF * 32];
-  float4 red[kNW][32];
+  unsigned short cand[kNW][kStageF];
+  unsigned short list[kNW][kLane * 32];
   int wcount[kNW];
 };
 
@@ -327,9 +329,9 @@ struct StageRange {
 
 // Stage the particles of this warp's share of the group's source leaves that
 // lie within R of the group box (R = Rg, or max(Rg, h_j) for the force). A
-// count pass sizes each warp's share, the warps' shares are laid out in warp
-// order, and a write pass fills them: block-wide capacity, deterministic order.
-// Must be called by every thread of the block. total > cap means overflow.
+// count pass sizes each warp's share, the shares are laid out in warp order,
+// and a write pass fills them. Called by every thread of the block.
+// total > cap means overflow.
 template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
@@ -340,6 +342,8 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   const float4 *pm = FORCE ? fa->pm : da->pm;
   StageRange r;
   r.base = 0;
+  r.count = 0;
+  r.total = 0;
   for (int write = 0; write < 2; ++write) {
     int nst = 0;
     for (int e = e0 + warp; e < e1; e += kNW) {
@@ -382,7 +386,6 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
     if (!write) {
       if (lane == 0) wcount[warp] = nst;
       __syncthreads();
-      r.total = 0;
       for (int w = 0; w < kNW; ++w) {
         if (w < warp) r.base += wcount[w];
         r.total += wcount[w];
@@ -396,14 +399,69 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   return r;
 }
 
+// Sub-cluster box of this warp's targets (lanes with has = false ignored):
+// every lane gets the min / max over the warp.
+__device__ __forceinline__ void sub_box(bool has, float px, float py, float pz, float lo[3],
+                                        float hi[3]) {
+  lo[0] = has ? px : 3e38f;
+  lo[1] = has ? py : 3e38f;
+  lo[2] = has ? pz : 3e38f;
+  hi[0] = has ? px : -3e38f;
+  hi[1] = has ? py : -3e38f;
+  hi[2] = has ? pz : -3e38f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o; o >>= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+}
+
+// Warp-wide filter of the stage: entries within R (R = Rsub, or for the
+// force max(Rsub, h_j)) of the sub-cluster box, compacted in stage order into
+// `cand`. Returns the count (> cap means overflow).
+template <bool FORCE>
+__device__ __forceinline__ int filter_stage(const float4 *sq, const float4 *sf, int nst,
+                                            const float lo[3], const float hi[3], float Rsub,
+                                            unsigned short *cand, int cap, int lane) {
+  const unsigned ltmask = (1u << lane) - 1u;
+  int n = 0;
+  for (int kb = 0; kb < nst; kb += 32) {
+    const int k = kb + lane;
+    bool in = false;
+    if (k < nst) {
+      const float4 q = sq[k];
+      const float R = FORCE ? fmaxf(Rsub, sf[k].x) : Rsub;
+      const float gx = fmaxf(0.f, fmaxf(lo[0] - q.x, q.x - hi[0]));
+      const float gy = fmaxf(0.f, fmaxf(lo[1] - q.y, q.y - hi[1]));
+      const float gz = fmaxf(0.f, fmaxf(lo[2] - q.z, q.z - hi[2]));
+      in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    const int pos = n + __popc(m & ltmask);
+    if (in && pos < cap) cand[pos] = (unsigned short)k;
+    n += __popc(m);
+  }
+  __syncwarp();
+  return n;
+}
+
+// Sum of a per-lane value over the kSlice lanes of one target, in fixed order.
+__device__ __forceinline__ float slice_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
 template <bool KAHAN>
 __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem &S = *reinterpret_cast<DensSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *stage = S.stage;
+  const int slice = lane & (kSlice - 1);
+  unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
-  unsigned long long cand = 0, inter = 0;
+  unsigned long long ntest = 0, inter = 0;
   int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0;
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
@@ -411,8 +469,21 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
     const BoxDev &B = a.boxes[G.box];
     const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
     const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
-    const bool has = lane < G.count;
-    const int i = G.start + lane;
+    const float Rg = fminf(G.hmax * a.skin_stage, wmin);
+    const StageRange sr = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane,
+                                             Rg, S.stage, nullptr, nullptr, S.wcount, kStageD);
+    stage_max = max(stage_max, sr.total);
+    if (sr.total > kStageD) {  // block-uniform: the whole group goes to the per-pass form
+      if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
+        ++fallback;
+      continue;
+    }
+    const int nst = sr.total;
+
+    // this warp's targets: lane = target * kSlice + slice
+    const int tloc = warp * kSub + (lane >> 2);
+    const bool has = tloc < G.count;
+    const int i = G.start + tloc;
     float px = 0.f, py = 0.f, pz = 0.f;
     HIter it;
     it.h = 1.0;
@@ -427,44 +498,50 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
       pz = q.z + (float)(L.o[2] - G.o[2]);
       it.h = a.h[i];
     }
-    const float Rg = fminf(G.hmax * a.skin_stage, wmin);
-    const StageRange sr = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane,
-                                             Rg, stage, nullptr, nullptr, S.wcount, kStageD);
-    stage_max = max(stage_max, sr.total);
-    bool failed = sr.total > kStageD;  // block-uniform
-    const int nst = min(sr.total, kStageD);
+    if (!__any_sync(0xffffffffu, has)) continue;  // this warp has no targets
+    float blo[3], bhi[3];
+    sub_box(has, px, py, pz, blo, bhi);
 
-    bool fin = !has, need = has;
-    int cnt = 0, passes = 0, ngb = 0;
-    float rl = 0.f;
+    bool failed = false, fin = !has, need_list = has, need_filter = true;
+    int ncand = 0, cnt = 0, passes = 0, ngb = 0;
+    float rsub = 0.f, rl = 0.f;
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int pass = 0; !failed && pass < a.max_iter; ++pass) {
-      // (re)build this warp's lists for lanes whose h outgrew the list radius
-      const bool bld = need && !fin;
-      if (__syncthreads_or(bld)) {
+    for (int pass = 0; pass < a.max_iter; ++pass) {
+      if (__any_sync(0xffffffffu, need_filter)) {
+        // sub-cluster radius: its largest h x the stage skin, capped by Rg
+        float hm = has && !fin ? (float)it.h : 0.f;
+        for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+        rsub = fminf(hm * a.skin_stage, Rg);
+        ncand = filter_stage<false>(S.stage, nullptr, nst, blo, bhi, rsub, cand, kStageD, lane);
+        need_filter = false;
+        need_list = !fin;
+      }
+      if (__any_sync(0xffffffffu, need_list)) {
         float rl2 = -1.f;
-        if (bld) {
-          rl = fminf((float)it.h * a.skin_list, Rg);
+        if (need_list) {
+          rl = fminf((float)it.h * a.skin_list, rsub);
           rl2 = rl * rl;
           cnt = 0;
-          cand += (nst + kNW - 1 - warp) / kNW;
+          ntest += (ncand + kSlice - 1 - slice) / kSlice;
         }
-        for (int k = warp; k < nst; k += kNW) {  // interleaved: balanced lists
-          const float4 q = stage[k];
+        for (int t = slice; t < ncand; t += kSlice) {
+          const int k = cand[t];
+          const float4 q = S.stage[k];
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (r2 < rl2) {
-            if (cnt < kListD) list[cnt * 32 + lane] = (unsigned short)k;
+            if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
             ++cnt;
           }
         }
-        need = false;
-        if (__syncthreads_or(cnt > kListD)) {
+        need_list = false;
+        if (__any_sync(0xffffffffu, cnt > kLane)) {
           failed = true;
           break;
         }
+        __syncwarp();
       }
-      // partial sums of this warp at the current h
+      // partial sums over this lane's slice at the current h
       const float hf = (float)it.h;
       const float h2 = fin ? -1.f : hf * hf;
       const float hinv = 1.f / hf;
@@ -474,7 +551,7 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
       const int tmax = warp_max_int(fin ? 0 : cnt);
       for (int t = 0; t < tmax; ++t) {
         if (t < cnt && !fin) {
-          const float4 q = stage[list[t * 32 + lane]];
+          const float4 q = S.stage[list[t * 32 + lane]];
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (r2 < h2) {
@@ -498,21 +575,11 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
           }
         }
       }
-      if (!fin) cand += cnt;
-      S.red[warp][lane] = make_float4(sw, sdw, smw, smdh);
-      S.redc[warp][lane] = c;
-      __syncthreads();
-      float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
-      int ctot = 0;
-      for (int w = 0; w < kNW; ++w) {  // fixed order: identical totals in every warp
-        const float4 r = S.red[w][lane];
-        tot.x += r.x;
-        tot.y += r.y;
-        tot.z += r.z;
-        tot.w += r.w;
-        ctot += S.redc[w][lane];
-      }
-      __syncthreads();
+      if (!fin) ntest += cnt;
+      const float4 tot = make_float4(slice_sum(sw), slice_sum(sdw), slice_sum(smw), slice_sum(smdh));
+      int ctot = c;
+      ctot += __shfl_xor_sync(0xffffffffu, ctot, 1);
+      ctot += __shfl_xor_sync(0xffffffffu, ctot, 2);
       if (!fin) {
         ++passes;
         int st = 0;
@@ -522,19 +589,23 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
           fin = true;
           fs = tot;
           ngb = ctot - 1;  // the self term is always inside
+        } else if ((float)it.h > rsub) {
+          need_filter = true;
         } else if ((float)it.h > rl) {
-          need = true;
+          need_list = true;
         }
       }
-      if (__syncthreads_or(!fin && (float)it.h > Rg)) failed = true;  // beyond the stage
-      if (__syncthreads_and(fin)) break;
+      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rg)) {
+        failed = true;  // beyond the staged radius
+        break;
+      }
+      if (__all_sync(0xffffffffu, fin)) break;
     }
-    const bool all_fin = __syncthreads_and(fin) != 0;
-    if (failed || !all_fin) {
-      if (warp == 0 && has) ++fallback;  // left to the per-pass form
+    if (failed || !__all_sync(0xffffffffu, fin)) {
+      if (has && slice == 0) ++fallback;  // left to the per-pass form
       continue;
     }
-    if (warp == 0 && has) {
+    if (has && slice == 0) {
       float rho, omega, P;
       float4 fi;
       const bool ok = finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi);
@@ -552,13 +623,13 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
       max_it = max(max_it, passes);
     }
   }
-  cand = warp_sum(cand);
+  ntest = warp_sum(ntest);
   inter = warp_sum(inter);
   fallback = (int)warp_sum((unsigned long long)fallback);
   max_it = warp_max_int(max_it);
   for (int o = 16; o; o >>= 1) st_bits |= __shfl_xor_sync(0xffffffffu, st_bits, o);
   if (lane == 0) {
-    if (cand) atomicAdd(&a.ctr->dens_cand, cand);
+    if (ntest) atomicAdd(&a.ctr->dens_cand, ntest);
     if (inter) atomicAdd(&a.ctr->dens_inter, inter);
     if (fallback) {
       atomicAdd(&a.ctr->unconverged, fallback);
@@ -594,17 +665,25 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4 *sq = S.sq;
-  float4 *sf = S.sf;
-  float4 *sv = S.sv;
+  const int slice = lane & (kSlice - 1);
+  unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
-  unsigned long long cand = 0, inter = 0;
+  unsigned long long ntest = 0, inter = 0;
   int fallback = 0, stage_max = 0;
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
-    const bool has = lane < G.count;
-    const int i = G.start + lane;
+    const StageRange sr = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
+                                            G.hmax, S.sq, S.sf, S.sv, S.wcount, kStageF);
+    stage_max = max(stage_max, sr.total);
+    if (sr.total > kStageF) {  // block-uniform
+      if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
+        ++fallback;
+      continue;
+    }
+    const int tloc = warp * kSub + (lane >> 2);
+    const bool has = tloc < G.count;
+    const int i = G.start + tloc;
     float px = 0.f, py = 0.f, pz = 0.f;
     float4 fi = make_float4(1.f, 1.f, 0.f, -1.f), vi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (has) {
@@ -616,37 +695,38 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
       fi = a.fi[i];
       vi = a.vu[i];
     }
+    if (!__any_sync(0xffffffffu, has)) continue;
+    float blo[3], bhi[3];
+    sub_box(has, px, py, pz, blo, bhi);
+    float hm = has ? fi.x : 0.f;
+    for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    const int ncand = filter_stage<true>(S.sq, S.sf, sr.total, blo, bhi, hm, cand, kStageF, lane);
     const float hi2 = has ? fi.w : -1.f;
-    const StageRange sr = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
-                                            G.hmax, sq, sf, sv, S.wcount, kStageF);
-    stage_max = max(stage_max, sr.total);
-    bool failed = sr.total > kStageF;  // block-uniform
     int cnt = 0;
-    if (!failed) {
-      for (int k = warp; k < sr.total; k += kNW) {  // interleaved: balanced lists
-        const float4 q = sq[k];
-        const float hj2 = sf[k].w;
-        const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-          if (cnt < kListF) list[cnt * 32 + lane] = (unsigned short)k;
-          ++cnt;
-        }
+    for (int t = slice; t < ncand; t += kSlice) {
+      const int k = cand[t];
+      const float4 q = S.sq[k];
+      const float hj2 = S.sf[k].w;
+      const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+        if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
+        ++cnt;
       }
-      if (has) cand += (sr.total + kNW - 1 - warp) / kNW;
-      failed = __syncthreads_or(cnt > kListF) != 0;
     }
-    if (failed) {
-      if (warp == 0 && has) ++fallback;
+    if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
+    if (__any_sync(0xffffffffu, cnt > kLane)) {
+      if (has && slice == 0) ++fallback;
       continue;
     }
+    __syncwarp();
     float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
     const int tmax = warp_max_int(has ? cnt : 0);
     for (int t = 0; t < tmax; ++t) {
       if (t < cnt) {
         const int k = list[t * 32 + lane];
-        const float4 q = sq[k];
-        const float4 f = sf[k];
+        const float4 q = S.sq[k];
+        const float4 f = S.sf[k];
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rinv = rsqrtf(r2);
@@ -654,7 +734,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
         const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
         const float tj = f.z * dw_only(r * f.y);    // A_j dW/dr(r, h_j)
         const float fac = q.w * (ti + tj) * rinv;
-        const float4 vj = sv[k];
+        const float4 vj = S.sv[k];
         const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
         ax = fmaf(-fac, dx, ax);
         ay = fmaf(-fac, dy, ay);
@@ -662,45 +742,26 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
         du = fmaf(q.w * ti * rinv, dvdx, du);
       }
     }
-    S.red[warp][lane] = make_float4(ax, ay, az, du);
+    ax = slice_sum(ax);
+    ay = slice_sum(ay);
+    az = slice_sum(az);
+    du = slice_sum(du);
     int ctot = cnt;
-    __syncthreads();
-    if (warp == 0) {
-      float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int w = 0; w < kNW; ++w) {
-        const float4 r = S.red[w][lane];
-        tot.x += r.x;
-        tot.y += r.y;
-        tot.z += r.z;
-        tot.w += r.w;
-      }
-      S.red[0][lane] = tot;  // warp 0 alone reads and writes its own row
-    }
-    // counts: every warp adds its own
-    if (has) {
-      inter += (unsigned long long)ctot;
-      cand += ctot;
-    }
-    __syncthreads();
-    if (warp == 0 && has) {
-      a.acc[i] = S.red[0][lane];
+    ctot += __shfl_xor_sync(0xffffffffu, ctot, 1);
+    ctot += __shfl_xor_sync(0xffffffffu, ctot, 2);
+    if (has) ntest += cnt;
+    if (has && slice == 0) {
+      a.acc[i] = make_float4(ax, ay, az, du);
+      a.nforce[i] = ctot;
       a.fdone[i] = 1;
+      inter += (unsigned long long)ctot;
     }
-    // per-particle count: sum over warps through the (now free) red rows
-    if (has) S.red[warp][lane].x = __int_as_float(ctot);
-    __syncthreads();
-    if (warp == 0 && has) {
-      int n = 0;
-      for (int w = 0; w < kNW; ++w) n += __float_as_int(S.red[w][lane].x);
-      a.nforce[i] = n;
-    }
-    __syncthreads();
   }
-  cand = warp_sum(cand);
+  ntest = warp_sum(ntest);
   inter = warp_sum(inter);
   fallback = (int)warp_sum((unsigned long long)fallback);
   if (lane == 0) {
-    if (cand) atomicAdd(&a.ctr->force_cand, cand);
+    if (ntest) atomicAdd(&a.ctr->force_cand, ntest);
     if (inter) atomicAdd(&a.ctr->force_inter, inter);
     if (fallback) {
       atomicAdd(&a.ctr->unconverged, fallback);

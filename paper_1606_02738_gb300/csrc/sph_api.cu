@@ -646,8 +646,8 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &off, DevBuf &t
   return sync_check(c);
 }
 
-constexpr float kSkinStage = 1.25f;  // staged radius = 1.25 x the group's largest h
-constexpr float kSkinList = 1.1f;    // per-lane list radius = 1.1 x the lane's h
+constexpr float kSkinStage = 1.15f;  // staged radius = 1.15 x the group's largest h
+constexpr float kSkinList = 1.05f;   // per-lane list radius = 1.05 x the lane's h
 
 // Batched density: every particle whose group fits the stage and converges
 // inside the kernel is finished here; the rest keep done = 0 for the
