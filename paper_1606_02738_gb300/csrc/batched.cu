@@ -303,22 +303,24 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
 constexpr int kNW = 4;           // warps per block, one group per block
 constexpr int kSub = 8;          // targets per warp
 constexpr int kSlice = 4;        // lanes per target
-constexpr int kStageD = 1536;    // density stage entries per group
-constexpr int kStageF = 896;     // force stage entries per group
+constexpr int kStageD = 1280;    // density stage entries per group
+constexpr int kStageF = 1024;    // force stage entries per group
+constexpr int kCandD = 768;      // density entries kept per warp
+constexpr int kCandF = 640;      // force entries kept per warp
 constexpr int kLane = 32;        // list entries per lane
 
 struct DensSmem {
   float4 stage[kStageD];                    // position in the group frame, m
-  unsigned short cand[kNW][kStageD];        // each warp's pre-filtered entries
+  unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][kLane * 32];     // [entry][lane]
   int wcount[kNW];
 };
 
 struct ForceSmem {
   float4 sq[kStageF];                       // position in the group frame, m
-  float4 sf[kStageF];                       // h, 1/h, A (8/pi) h^-4, h^2
-  float4 sv[kStageF];                       // v, u
-  unsigned short cand[kNW][kStageF];
+  float2 sf[kStageF];                       // A (8/pi) h^-4, h^2
+  int sj[kStageF];                          // particle index (velocity read on use)
+  unsigned short cand[kNW][kCandF];
   unsigned short list[kNW][kLane * 32];
   int wcount[kNW];
 };
@@ -335,7 +337,7 @@ struct StageRange {
 template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
-                                  float4 *sq, float4 *sf, float4 *sv, int *wcount, int cap) {
+                                  float4 *sq, float2 *sf, int *sj, int *wcount, int cap) {
   const unsigned ltmask = (1u << lane) - 1u;
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
@@ -375,8 +377,8 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
           if (in && pos < cap) {
             sq[pos] = q;
             if (FORCE) {
-              sf[pos] = f;
-              sv[pos] = fa->vu[j];
+              sf[pos] = make_float2(f.z, f.w);
+              sj[pos] = j;
             }
           }
         }
@@ -421,7 +423,7 @@ __device__ __forceinline__ void sub_box(bool has, float px, float py, float pz, 
 // force max(Rsub, h_j)) of the sub-cluster box, compacted in stage order into
 // `cand`. Returns the count (> cap means overflow).
 template <bool FORCE>
-__device__ __forceinline__ int filter_stage(const float4 *sq, const float4 *sf, int nst,
+__device__ __forceinline__ int filter_stage(const float4 *sq, const float2 *sf, int nst,
                                             const float lo[3], const float hi[3], float Rsub,
                                             unsigned short *cand, int cap, int lane) {
   const unsigned ltmask = (1u << lane) - 1u;
@@ -431,7 +433,7 @@ __device__ __forceinline__ int filter_stage(const float4 *sq, const float4 *sf, 
     bool in = false;
     if (k < nst) {
       const float4 q = sq[k];
-      const float R = FORCE ? fmaxf(Rsub, sf[k].x) : Rsub;
+      const float R = FORCE ? fmaxf(Rsub, sqrtf(sf[k].y)) : Rsub;
       const float gx = fmaxf(0.f, fmaxf(lo[0] - q.x, q.x - hi[0]));
       const float gy = fmaxf(0.f, fmaxf(lo[1] - q.y, q.y - hi[1]));
       const float gz = fmaxf(0.f, fmaxf(lo[2] - q.z, q.z - hi[2]));
@@ -454,7 +456,7 @@ __device__ __forceinline__ float slice_sum(float v) {
 }
 
 template <bool KAHAN>
-__global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
+__global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem &S = *reinterpret_cast<DensSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -512,9 +514,13 @@ __global__ void __launch_bounds__(kNW * 32) k_density_batched(BatchDensArgs a) {
         float hm = has && !fin ? (float)it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
         rsub = fminf(hm * a.skin_stage, Rg);
-        ncand = filter_stage<false>(S.stage, nullptr, nst, blo, bhi, rsub, cand, kStageD, lane);
+        ncand = filter_stage<false>(S.stage, nullptr, nst, blo, bhi, rsub, cand, kCandD, lane);
         need_filter = false;
         need_list = !fin;
+        if (__any_sync(0xffffffffu, ncand > kCandD)) {
+          failed = true;
+          break;
+        }
       }
       if (__any_sync(0xffffffffu, need_list)) {
         float rl2 = -1.f;
@@ -661,7 +667,7 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   note_launch();
 }
 
-__global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
+__global__ void __launch_bounds__(kNW * 32, 6) k_force_batched(BatchForceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -674,7 +680,7 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
     const StageRange sr = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
-                                            G.hmax, S.sq, S.sf, S.sv, S.wcount, kStageF);
+                                            G.hmax, S.sq, S.sf, S.sj, S.wcount, kStageF);
     stage_max = max(stage_max, sr.total);
     if (sr.total > kStageF) {  // block-uniform
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
@@ -700,13 +706,17 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
     sub_box(has, px, py, pz, blo, bhi);
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-    const int ncand = filter_stage<true>(S.sq, S.sf, sr.total, blo, bhi, hm, cand, kStageF, lane);
+    const int ncand = filter_stage<true>(S.sq, S.sf, sr.total, blo, bhi, hm, cand, kCandF, lane);
+    if (__any_sync(0xffffffffu, ncand > kCandF)) {
+      if (has && slice == 0) ++fallback;
+      continue;
+    }
     const float hi2 = has ? fi.w : -1.f;
     int cnt = 0;
     for (int t = slice; t < ncand; t += kSlice) {
       const int k = cand[t];
       const float4 q = S.sq[k];
-      const float hj2 = S.sf[k].w;
+      const float hj2 = S.sf[k].y;
       const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
@@ -726,15 +736,15 @@ __global__ void __launch_bounds__(kNW * 32) k_force_batched(BatchForceArgs a) {
       if (t < cnt) {
         const int k = list[t * 32 + lane];
         const float4 q = S.sq[k];
-        const float4 f = S.sf[k];
+        const float2 f = S.sf[k];
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rinv = rsqrtf(r2);
         const float r = r2 * rinv;
         const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
-        const float tj = f.z * dw_only(r * f.y);    // A_j dW/dr(r, h_j)
+        const float tj = f.x * dw_only(r * rsqrtf(f.y));  // A_j dW/dr(r, h_j)
         const float fac = q.w * (ti + tj) * rinv;
-        const float4 vj = S.sv[k];
+        const float4 vj = a.vu[S.sj[k]];
         const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
         ax = fmaf(-fac, dx, ax);
         ay = fmaf(-fac, dy, ay);

@@ -138,7 +138,10 @@ __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, d
   const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
   double hn = s_ln > 0.0 ? h * exp(log(n_ngb / N) / s_ln) : 2.0 * h;
   hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
-  if (hi < 1e300 && (!(hn > lo && hn < hi) || fabs(f) > 0.5 * (double)it.fprev))
+  // (the halving test applies only well above the FP32 noise of the sums,
+  // where |f| cannot be expected to halve)
+  if (hi < 1e300 && (!(hn > lo && hn < hi) ||
+                     (fabs(f) > 0.5 * (double)it.fprev && fabs(f) > 1e-4 * n_ngb)))
     hn = 0.5 * (lo + hi);
   it.fprev = (float)fabs(f);
   if (hn > hcap) {
