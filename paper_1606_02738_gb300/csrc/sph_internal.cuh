@@ -119,15 +119,16 @@ struct HIter {
 // from the FP32 sums `s` at h. Returns true when h is accepted: |N - n_ngb| <=
 // tol n_ngb, or the next step would move h by at most 5e-7 h (the resolution
 // of FP32 sums). Otherwise moves h by Newton on ln N(ln h) (exponent
-// s = h N'/N measured, so steep N near clusters does not overshoot), clamped
-// to [h/8, 2h] and to hcap (L/3), bisecting the bracket when the step leaves
-// it or |f| failed to halve. *st receives kErrBoxTooSmall when the root lies
-// beyond hcap.
+// s = h N'/N = -(sum q w') / (sum w) measured, so steep N near clusters does
+// not overshoot), clamped to [h/8, 2h] and to hcap (L/3), bisecting the
+// bracket when the step leaves it or |f| failed to halve well above the FP32
+// noise. *st receives kErrBoxTooSmall when the root lies beyond hcap.
+// The bracket and h are FP64; the step factor is FP32 (a proposal that the
+// next pass corrects; FP64 exp/log/division are slow on this part).
 __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, double n_ngb,
                                               double tol, double hcap, int *st) {
   const double h = it.h;
   const double N = (32.0 / 3.0) * (double)sw;
-  const double dN = -(32.0 / (3.0 * h)) * (double)sqdw;
   const double f = N - n_ngb;
   if (fabs(f) <= tol * n_ngb) return true;
   double lo = it.lo, hi = it.hi;
@@ -135,11 +136,11 @@ __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, d
     lo = h;
   else
     hi = h;
-  const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
-  double hn = s_ln > 0.0 ? h * exp(log(n_ngb / N) / s_ln) : 2.0 * h;
-  hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
-  // (the halving test applies only well above the FP32 noise of the sums,
-  // where |f| cannot be expected to halve)
+  const float s_ln = sw > 0.f ? -sqdw / sw : 0.f;  // d ln N / d ln h
+  float fac = 2.f;
+  if (s_ln > 0.f) fac = __expf(__logf((float)n_ngb / ((32.f / 3.f) * sw)) / s_ln);
+  fac = fminf(fmaxf(fac, 0.125f), 2.f);
+  double hn = h * (double)fac;
   if (hi < 1e300 && (!(hn > lo && hn < hi) ||
                      (fabs(f) > 0.5 * (double)it.fprev && fabs(f) > 1e-4 * n_ngb)))
     hn = 0.5 * (lo + hi);
@@ -159,22 +160,24 @@ __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, d
 // (sum w, sum q w', sum m w, sum m (3w + q w')) and the internal energy u:
 // rho (Eq. rho), Omega = 1 + h/(3 rho) drho/dh, P = (gamma - 1) rho u, and the
 // force-stage record (h, 1/h, A (8/pi) h^-4, h^2) with A = P / (Omega rho^2).
+// FP32 arithmetic (relative error ~1e-7).
 __device__ __forceinline__ bool finalise_density(double h, float4 s, double u, double gamma,
                                                  float *rho_o, float *omega_o, float *P_o,
                                                  float4 *fi_o) {
-  const double pi = 3.14159265358979323846;
-  const double h2 = h * h;
-  const double rho = 8.0 / pi * (double)s.z / (h2 * h);
-  const double drho = -8.0 / pi * (double)s.w / (h2 * h2);
-  const double omega = 1.0 + h / (3.0 * rho) * drho;
-  const double P = (gamma - 1.0) * rho * u;
-  const double A = P / (omega * rho * rho);
-  *rho_o = (float)rho;
-  *omega_o = (float)omega;
-  *P_o = (float)P;
+  const float c8pi = 2.546479089470325f;  // 8 / pi
   const float hf = (float)h;
-  *fi_o = make_float4(hf, (float)(1.0 / h), (float)(A * 8.0 / pi / (h2 * h2)), hf * hf);
-  return rho > 0.0 && omega > 0.0 && u >= 0.0;
+  const float hinv = 1.f / hf;
+  const float hinv3 = hinv * hinv * hinv;
+  const float rho = c8pi * s.z * hinv3;
+  const float drho = -c8pi * s.w * hinv3 * hinv;
+  const float omega = 1.f + hf / (3.f * rho) * drho;
+  const float P = (float)(gamma - 1.0) * rho * (float)u;
+  const float A = P / (omega * rho * rho);
+  *rho_o = rho;
+  *omega_o = omega;
+  *P_o = P;
+  *fi_o = make_float4(hf, hinv, A * c8pi * hinv3 * hinv, hf * hf);
+  return rho > 0.f && omega > 0.f && u >= 0.0;
 }
 
 // Target group of the batched kernels: up to 32 consecutive particles (sorted
