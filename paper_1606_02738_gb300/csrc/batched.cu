@@ -224,68 +224,119 @@ void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s) {
   note_launch();
 }
 
-// One thread per group: the source leaves within the group's radius, found by
-// walking the octrees of the 27 neighbouring top cells (periodic). Count pass
-// when a.tasks is null, fill pass otherwise.
-__global__ void k_group_lists(GroupListArgs a) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n_groups) return;
+// One warp per group: the source leaves within the group's radius, found by
+// a breadth-first walk of the octrees of the 27 neighbouring top cells
+// (periodic). The lanes test 32 frontier nodes at a time; passing leaves are
+// written, in walk order, straight into the group's task slots, passing
+// inner nodes put their 8 children on the next frontier. Radius: for the
+// density, min(skin hmax_G, top-cell width); for the force, max(hmax_G,
+// hmax_S). count[g] > tcap marks an overflow (the group is then left to the
+// per-pass form).
+constexpr int kWalkWarps = 4;
+constexpr int kFront = 512;
+
+__global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a) {
+  __shared__ int2 front_all[kWalkWarps][2][kFront];  // (node, neighbour code 0..26)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned ltmask = (1u << lane) - 1u;
+  const int g = blockIdx.x * kWalkWarps + warp;
+  if (g >= a.n_groups) return;  // warp-uniform
+  int2 *cur = front_all[warp][0], *nxt = front_all[warp][1];
   const Group G = a.groups[g];
   const BoxDev &B = a.boxes[G.box];
   int c[3];
   cell_xyz(B, G.cell - B.cell_base, c);
   const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
   const float capG = a.force ? G.hmax : fminf(G.hmax * a.skin, wmin);
-  const bool fill = a.tasks != nullptr;
-  const int base = fill ? a.offset[g] : 0;
-  int cnt = 0;
-  int stack[kWalkStack];
-  for (int dx = -1; dx <= 1; ++dx)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
-                           (c[2] + dz + B.n[2]) % B.n[2]};
-        const int cellS = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
-        const double shd[3] = {dx * B.w[0], dy * B.w[1], dz * B.w[2]};
-        const float sh[3] = {(float)shd[0], (float)shd[1], (float)shd[2]};
-        int top = 0;
-        stack[top++] = cellS;
-        while (top > 0) {
-          const int id = stack[--top];
-          const Node &S = a.nodes[id];
-          if (S.count == 0) continue;
+  Task *out = a.tasks + (size_t)g * a.tcap;
+
+  // frontier 0: the 27 neighbouring top cells
+  int n = 0;
+  {
+    bool in = lane < 27;
+    int2 e = make_int2(0, lane);
+    if (in) {
+      const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+      const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                         (c[2] + dz + B.n[2]) % B.n[2]};
+      e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) cur[__popc(m & ltmask)] = e;
+    n = __popc(m);
+  }
+  __syncwarp();
+  int ntask = 0;
+  bool overflow = false;
+  while (n > 0) {
+    int nn = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int idx = base + lane;
+      bool leaf_in = false, inner_in = false;
+      int node = 0, code = 0, child = 0, leaf = 0;
+      if (idx < n) {
+        const int2 e = cur[idx];
+        node = e.x;
+        code = e.y;
+        const Node &S = a.nodes[node];
+        if (S.count > 0) {
+          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+          const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
           float d2 = 0.f;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float gap = fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - G.thi[d], G.tlo[d] - S.hi[d] - sh[d]));
+            const float gap =
+                fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - G.thi[d], G.tlo[d] - S.hi[d] - sh[d]));
             d2 = fmaf(gap, gap, d2);
           }
           const float crit = (a.force ? fmaxf(capG, S.hmax) : capG) + B.eps;
-          if (d2 >= crit * crit) continue;
-          if (S.child < 0) {
-            if (fill) {
-              const Leaf &LS = a.leaves[S.leaf];
-              Task tk;
-              tk.sx = (float)(LS.o[0] + shd[0] - G.o[0]);
-              tk.sy = (float)(LS.o[1] + shd[1] - G.o[1]);
-              tk.sz = (float)(LS.o[2] + shd[2] - G.o[2]);
-              tk.src = S.leaf;
-              a.tasks[base + cnt] = tk;
-            }
-            ++cnt;
-          } else if (top + 8 <= kWalkStack) {
-            for (int o = 7; o >= 0; --o) stack[top++] = S.child + o;
-          } else {
-            atomicOr(a.status, kErrListOverflow);
+          if (d2 < crit * crit) {
+            child = S.child;
+            leaf = S.leaf;
+            leaf_in = child < 0;
+            inner_in = child >= 0;
           }
         }
       }
-  if (!fill) a.count[g] = cnt;
+      const unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
+      if (leaf_in) {
+        const int pos = ntask + __popc(ml & ltmask);
+        if (pos < a.tcap) {
+          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+          const Leaf &LS = a.leaves[leaf];
+          Task tk;
+          tk.sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
+          tk.sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
+          tk.sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
+          tk.src = leaf;
+          out[pos] = tk;
+        }
+      }
+      ntask += __popc(ml);
+      const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
+      if (inner_in) {
+        const int pos = nn + 8 * __popc(mi & ltmask);
+        for (int o = 0; o < 8; ++o)
+          if (pos + o < kFront) nxt[pos + o] = make_int2(child + o, code);
+      }
+      nn += 8 * __popc(mi);
+    }
+    __syncwarp();
+    if (nn > kFront) {
+      overflow = true;
+      break;
+    }
+    int2 *t = cur;
+    cur = nxt;
+    nxt = t;
+    n = nn;
+  }
+  if (lane == 0) a.count[g] = overflow ? a.tcap + 1 : ntask;
 }
 
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  k_group_lists<<<(a.n_groups + 127) / 128, 128, 0, s>>>(a);
+  k_group_walk<<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a);
   note_launch();
 }
 
@@ -472,10 +523,12 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
     const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
     const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
-    const StageRange sr = stage_group<false>(&a, nullptr, G, a.off[g], a.off[g + 1], warp, lane,
+    const int nt = a.tcount[g];
+    const int e0 = g * a.tcap;
+    const StageRange sr = stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane,
                                              Rg, S.stage, nullptr, nullptr, S.wcount, kStageD);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > kStageD) {  // block-uniform: the whole group goes to the per-pass form
+    if (sr.total > kStageD || nt > a.tcap) {  // block-uniform: the group goes to the per-pass form
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
         ++fallback;
       continue;
@@ -679,10 +732,12 @@ __global__ void __launch_bounds__(kNW * 32, 6) k_force_batched(BatchForceArgs a)
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
-    const StageRange sr = stage_group<true>(nullptr, &a, G, a.off[g], a.off[g + 1], warp, lane,
+    const int nt = a.tcount[g];
+    const int e0 = g * a.tcap;
+    const StageRange sr = stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane,
                                             G.hmax, S.sq, S.sf, S.sj, S.wcount, kStageF);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > kStageF) {  // block-uniform
+    if (sr.total > kStageF || nt > a.tcap) {  // block-uniform
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
         ++fallback;
       continue;

@@ -612,12 +612,15 @@ int build_groups(sph_ctx *c) {
   return sync_check(c);
 }
 
-// Group task lists: count pass, scan, fill pass.
-int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &off, DevBuf &tasks,
-                      int64_t &n_tasks) {
+constexpr int kTaskCap = 384;  // task slots per group
+
+// Group task lists: one walk, written into fixed per-group slots (no host
+// round trip).
+int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &tasks) {
   tic(c, kLists);
   const int ng = c->n_groups;
-  TRY(ensure(c, off, sizeof(int) * (size_t)(ng + 1)));
+  TRY(ensure(c, cnt, sizeof(int) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(ng, 1) * kTaskCap));
   GroupListArgs la{};
   la.n_groups = ng;
   la.groups = as<Group>(c->groups);
@@ -626,22 +629,11 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &off, DevBuf &t
   la.boxes = c->boxes_d;
   la.force = force ? 1 : 0;
   la.skin = skin;
-  la.count = as<int>(off);
-  la.status = &c->ctr->status;
-  CUDA_TRY(cudaMemsetAsync(as<int>(off) + ng, 0, sizeof(int), c->stream));
-  launch_group_lists(la, c->stream);
-  exclusive_scan_int(as<int>(off), as<int>(off), ng + 1, c->scan_tmp.p, c->scan_tmp.bytes,
-                     c->stream);
-  int total = 0;
-  CUDA_TRY(cudaMemcpyAsync(&total, as<int>(off) + ng, sizeof(int), cudaMemcpyDeviceToHost,
-                           c->stream));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  if (total < 0) return fail(c, SPH_ENOMEM, "task list exceeds 2^31 entries");
-  TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(total, 1)));
-  la.offset = as<int>(off);
+  la.tcap = kTaskCap;
+  la.count = as<int>(cnt);
   la.tasks = as<Task>(tasks);
+  la.status = &c->ctr->status;
   launch_group_lists(la, c->stream);
-  n_tasks = total;
   toc(c, kLists);
   return sync_check(c);
 }
@@ -658,11 +650,12 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   launch_group_hmax(ga, c->stream);
   GeomArgs gg = geom_args(c);
   launch_leaf_hmax(gg, c->n_nodes, c->stream);
-  TRY(build_group_lists(c, false, kSkinStage, c->gd_off, c->gd_tasks, c->n_gd_tasks));
+  TRY(build_group_lists(c, false, kSkinStage, c->gd_off, c->gd_tasks));
   BatchDensArgs da{};
   da.n_groups = c->n_groups;
   da.groups = as<Group>(c->groups);
-  da.off = as<int>(c->gd_off);
+  da.tcount = as<int>(c->gd_off);
+  da.tcap = kTaskCap;
   da.tasks = as<Task>(c->gd_tasks);
   da.leaves = as<Leaf>(c->leaves);
   da.leaf_of = c->leaf_of;
@@ -805,7 +798,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   launch_group_hmax(gb, c->stream);
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
-  TRY(build_group_lists(c, true, 1.0f, c->gf_off, c->gf_tasks, c->n_gf_tasks));
+  TRY(build_group_lists(c, true, 1.0f, c->gf_off, c->gf_tasks));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
@@ -813,7 +806,8 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
   fa.groups = as<Group>(c->groups);
-  fa.off = as<int>(c->gf_off);
+  fa.tcount = as<int>(c->gf_off);
+  fa.tcap = kTaskCap;
   fa.tasks = as<Task>(c->gf_tasks);
   fa.leaves = as<Leaf>(c->leaves);
   fa.leaf_of = c->leaf_of;

@@ -362,9 +362,9 @@ struct GroupListArgs {
   const BoxDev *boxes;
   int force;             // 0: density stage radius, 1: max(hmax_G, hmax_S)
   float skin;            // density stage radius = min(skin * hmax_G, top-cell width)
-  int *count;            // [n_groups + 1]
-  const int *offset;
-  Task *tasks;
+  int tcap;              // task slots per group
+  int *count;            // [n_groups] tasks found (> tcap: overflow)
+  Task *tasks;           // [n_groups * tcap]
   int *status;
 };
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
@@ -372,7 +372,8 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
 struct BatchDensArgs {
   int n_groups;
   const Group *groups;
-  const int *off;
+  const int *tcount;     // tasks of group g: tasks[g * tcap + k], k < tcount[g]
+  int tcap;
   const Task *tasks;
   const Leaf *leaves;
   const int *leaf_of;
@@ -397,7 +398,8 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 struct BatchForceArgs {
   int n_groups;
   const Group *groups;
-  const int *off;
+  const int *tcount;
+  int tcap;
   const Task *tasks;
   const Leaf *leaves;
   const int *leaf_of;
