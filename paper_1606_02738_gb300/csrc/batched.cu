@@ -356,7 +356,7 @@ constexpr int kSub = 8;          // targets per warp
 constexpr int kSlice = 4;        // lanes per target
 constexpr int kStageD = 1280;    // density stage entries per group
 constexpr int kStageF = 1024;    // force stage entries per group
-constexpr int kCandD = 768;      // density entries kept per warp
+constexpr int kCandD = 1280;     // density entries kept per warp
 constexpr int kCandF = 640;      // force entries kept per warp
 constexpr int kLane = 32;        // list entries per lane
 
