@@ -381,10 +381,14 @@ struct StageRange {
 };
 
 // Stage the particles of this warp's share of the group's source leaves that
-// lie within R of the group box (R = Rg, or max(Rg, h_j) for the force). A
-// count pass sizes each warp's share, the shares are laid out in warp order,
-// and a write pass fills them. Called by every thread of the block.
-// total > cap means overflow.
+// lie within R of the group box (R = Rg, or max(Rg, h_j) for the force). The
+// warp takes 32 of its tasks at a time, one per lane; a warp scan of their
+// particle counts gives each task's offset, and the lanes then walk the
+// concatenated particles 32 at a time (a particle finds its task by a 5-step
+// shuffle search), so lanes stay busy however small the leaves are. A count
+// pass sizes each warp's share, the shares are laid out in warp order, and a
+// write pass fills them: the stage order never depends on timing. Called by
+// every thread of the block; total > cap means overflow.
 template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
@@ -393,29 +397,59 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
   const float4 *pm = FORCE ? fa->pm : da->pm;
+  const int ntask = e1 - e0;
   StageRange r;
   r.base = 0;
   r.count = 0;
   r.total = 0;
   for (int write = 0; write < 2; ++write) {
     int nst = 0;
-    for (int e = e0 + warp; e < e1; e += kNW) {
-      const Task tk = tasks[e];
-      const Leaf &LS = leaves[tk.src];
-      const int js = LS.start, jn = LS.count;
-      for (int jb = 0; jb < jn; jb += 32) {
+    for (int tb = warp; tb < ntask; tb += 32 * kNW) {
+      const int mt = tb + lane * kNW;  // this lane's task
+      int start = 0, cnt = 0;
+      float sx = 0.f, sy = 0.f, sz = 0.f;
+      if (mt < ntask) {
+        const Task tk = tasks[e0 + mt];
+        const Leaf &LS = leaves[tk.src];
+        start = LS.start;
+        cnt = LS.count;
+        sx = tk.sx;
+        sy = tk.sy;
+        sz = tk.sz;
+      }
+      int incl = cnt;  // inclusive scan over the lanes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        int t = 0;  // first task whose inclusive count exceeds f
+#pragma unroll
+        for (int s = 16; s; s >>= 1) {
+          const int v = __shfl_sync(0xffffffffu, incl, t + s - 1);
+          if (v <= f) t += s;
+        }
+        const int t_incl = __shfl_sync(0xffffffffu, incl, t);
+        const int t_cnt = __shfl_sync(0xffffffffu, cnt, t);
+        const int t_start = __shfl_sync(0xffffffffu, start, t);
+        const float tx = __shfl_sync(0xffffffffu, sx, t);
+        const float ty = __shfl_sync(0xffffffffu, sy, t);
+        const float tz = __shfl_sync(0xffffffffu, sz, t);
         bool in = false;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), f = q;
-        const int j = js + jb + lane;
-        if (jb + lane < jn) {
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), fj = q;
+        const int j = t_start + f - (t_incl - t_cnt);
+        if (f < total) {
           q = pm[j];
-          q.x += tk.sx;
-          q.y += tk.sy;
-          q.z += tk.sz;
+          q.x += tx;
+          q.y += ty;
+          q.z += tz;
           float R = Rg;
           if (FORCE) {
-            f = fa->fi[j];
-            R = fmaxf(Rg, f.x);
+            fj = fa->fi[j];
+            R = fmaxf(Rg, fj.x);
           }
           const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
           const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
@@ -428,7 +462,7 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
           if (in && pos < cap) {
             sq[pos] = q;
             if (FORCE) {
-              sf[pos] = make_float2(f.z, f.w);
+              sf[pos] = make_float2(fj.z, fj.w);
               sj[pos] = j;
             }
           }
