@@ -424,50 +424,61 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
         if (lane >= o) incl += y;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
-      for (int f0 = 0; f0 < total; f0 += 32) {
-        const int f = f0 + lane;
-        int t = 0;  // first task whose inclusive count exceeds f
+      constexpr int kU = 4;  // chunks whose loads are in flight together
+      for (int f0 = 0; f0 < total; f0 += 32 * kU) {
+        float4 q[kU], fj[kU];
+        int jj[kU];
 #pragma unroll
-        for (int s = 16; s; s >>= 1) {
-          const int v = __shfl_sync(0xffffffffu, incl, t + s - 1);
-          if (v <= f) t += s;
-        }
-        const int t_incl = __shfl_sync(0xffffffffu, incl, t);
-        const int t_cnt = __shfl_sync(0xffffffffu, cnt, t);
-        const int t_start = __shfl_sync(0xffffffffu, start, t);
-        const float tx = __shfl_sync(0xffffffffu, sx, t);
-        const float ty = __shfl_sync(0xffffffffu, sy, t);
-        const float tz = __shfl_sync(0xffffffffu, sz, t);
-        bool in = false;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), fj = q;
-        const int j = t_start + f - (t_incl - t_cnt);
-        if (f < total) {
-          q = pm[j];
-          q.x += tx;
-          q.y += ty;
-          q.z += tz;
-          float R = Rg;
-          if (FORCE) {
-            fj = fa->fi[j];
-            R = fmaxf(Rg, fj.x);
+        for (int u = 0; u < kU; ++u) {
+          const int f = f0 + 32 * u + lane;
+          int t = 0;  // first task whose inclusive count exceeds f
+#pragma unroll
+          for (int s = 16; s; s >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, t + s - 1);
+            if (v <= f) t += s;
           }
-          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q.x, q.x - G.fhi[0]));
-          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q.y, q.y - G.fhi[1]));
-          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q.z, q.z - G.fhi[2]));
-          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+          const int t_incl = __shfl_sync(0xffffffffu, incl, t);
+          const int t_cnt = __shfl_sync(0xffffffffu, cnt, t);
+          const int t_start = __shfl_sync(0xffffffffu, start, t);
+          const float tx = __shfl_sync(0xffffffffu, sx, t);
+          const float ty = __shfl_sync(0xffffffffu, sy, t);
+          const float tz = __shfl_sync(0xffffffffu, sz, t);
+          jj[u] = t_start + f - (t_incl - t_cnt);
+          q[u] = make_float4(tx, ty, tz, 0.f);
+          fj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (f < total) {
+            const float4 p4 = pm[jj[u]];
+            q[u].x += p4.x;
+            q[u].y += p4.y;
+            q[u].z += p4.z;
+            q[u].w = p4.w;
+            if (FORCE) fj[u] = fa->fi[jj[u]];
+          }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (write) {
-          const int pos = r.base + nst + __popc(m & ltmask);
-          if (in && pos < cap) {
-            sq[pos] = q;
-            if (FORCE) {
-              sf[pos] = make_float2(fj.z, fj.w);
-              sj[pos] = j;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int f = f0 + 32 * u + lane;
+          bool in = false;
+          if (f < total) {
+            const float R = FORCE ? fmaxf(Rg, fj[u].x) : Rg;
+            const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q[u].x, q[u].x - G.fhi[0]));
+            const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q[u].y, q[u].y - G.fhi[1]));
+            const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q[u].z, q[u].z - G.fhi[2]));
+            in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (write) {
+            const int pos = r.base + nst + __popc(m & ltmask);
+            if (in && pos < cap) {
+              sq[pos] = q[u];
+              if (FORCE) {
+                sf[pos] = make_float2(fj[u].z, fj[u].w);
+                sj[pos] = jj[u];
+              }
             }
           }
+          nst += __popc(m);
         }
-        nst += __popc(m);
       }
     }
     if (!write) {
@@ -617,6 +628,7 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
           cnt = 0;
           ntest += (ncand + kSlice - 1 - slice) / kSlice;
         }
+#pragma unroll 4
         for (int t = slice; t < ncand; t += kSlice) {
           const int k = cand[t];
           const float4 q = S.stage[k];
@@ -754,7 +766,7 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   note_launch();
 }
 
-__global__ void __launch_bounds__(kNW * 32, 6) k_force_batched(BatchForceArgs a) {
+__global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -802,6 +814,7 @@ __global__ void __launch_bounds__(kNW * 32, 6) k_force_batched(BatchForceArgs a)
     }
     const float hi2 = has ? fi.w : -1.f;
     int cnt = 0;
+#pragma unroll 4
     for (int t = slice; t < ncand; t += kSlice) {
       const int k = cand[t];
       const float4 q = S.sq[k];
