@@ -431,13 +431,15 @@ static int solve_h(const finder *f, int64_t i, double h0, double n_ngb, double t
   double R = h0 > 0 ? h0 : Rmax * 0.01;
   if (R > Rmax) R = Rmax;
   double lo = 0.0;      /* N(lo) < n_ngb known */
-  int64_t limit = 4096; /* candidate cap while R may be far too large */
+  int64_t limit = 1024; /* candidate cap while R may be far too large */
   for (int guard = 0; guard < 400; ++guard) {
     int rc = collect(f, i, R, b, limit);
     if (rc) return rc;
     if (b->overflow) {
-      if (0.5 * R > lo) {
-        R *= 0.5;
+      /* far more candidates than a root radius holds: shrink the search
+       * radius (the root is unique, so only the search path changes) */
+      if (0.35 * R > lo) {
+        R *= 0.35;
       } else {
         limit = 0;
       }
