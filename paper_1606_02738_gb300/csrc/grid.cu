@@ -467,6 +467,40 @@ void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s) {
   k_leaf_hmax<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a); note_launch();
 }
 
+// Starting guess for the h iteration from the number density of each octree
+// leaf cell, n = count / cell volume: h_est = (3 n_ngb / (4 pi n))^(1/3),
+// capped below the top-cell width and L/3. A particle keeps its own h unless
+// that is more than 2x away from h_est (the root does not depend on where the
+// iteration starts; a near guess, e.g. the previous step's h, is kept).
+__global__ void k_h_guess(GeomArgs a, double n_ngb, double *h, float *hf) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= a.n_leaves) return;
+  const Leaf L = a.leaves[li];
+  const Node &nd = a.nodes[L.node];
+  const BoxDev &B = a.boxes[L.box];
+  const double scale = 1.0 / (double)(1 << nd.level);
+  const double vol = B.w[0] * scale * B.w[1] * scale * B.w[2] * scale;
+  const double n = (double)L.count / vol;
+  double est = cbrt(3.0 * n_ngb / (4.0 * 3.14159265358979323846 * n));
+  const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
+  const double lmin = fmin(B.L[0], fmin(B.L[1], B.L[2]));
+  est = fmin(est, fmin(wmin, lmin / 3.0) / (1.0 + 1e-5));
+  for (int k = 0; k < L.count; ++k) {
+    const int s = L.start + k;
+    const double hs = h[s];
+    if (hs > 2.0 * est || hs < 0.5 * est) {
+      h[s] = est;
+      hf[s] = (float)est;
+    }
+  }
+}
+
+void launch_h_guess(const GeomArgs &a, double n_ngb, double *h, float *hf, cudaStream_t s) {
+  if (a.n_leaves <= 0) return;
+  k_h_guess<<<(a.n_leaves + 127) / 128, 128, 0, s>>>(a, n_ngb, h, hf);
+  note_launch();
+}
+
 // ------------------------------------------------------------ task lists
 
 constexpr int kWalkStack = 96;

@@ -692,6 +692,7 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
 int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   if (!c->grid_valid) TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
   const int n = c->n;
+  launch_h_guess(geom_args(c), c->p.n_ngb, c->st.h, c->hf, c->stream);
   launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   c->last_passes = 0;

@@ -243,6 +243,7 @@ struct GeomArgs {
 };
 void launch_leaf_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s);
 void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s);
+void launch_h_guess(const GeomArgs &a, double n_ngb, double *h, float *hf, cudaStream_t s);
 
 // per-box largest h (dmax[nb]) and global min / max (dminmax[2]), as ordered
 // int64 bit patterns of non-negative doubles (dminmax[0] holds the minimum)

@@ -201,18 +201,24 @@ def clustered(n: int = 4194304, n_spheres: int = 64, frac_clustered: float = 0.7
 
 
 def batched(n_boxes: int = 256, n_min: int = 1024, n_max: int = 262144,
-            seed: int = SEED_BASE + 4, name: str = "batched") -> ParticleSet:
+            seed: int = SEED_BASE + 4, name: str = "batched",
+            min_clustered: int = 4096) -> ParticleSet:
     """Independent periodic unit boxes; box b holds
     N_b = round(exp(U(ln n_min, ln n_max))) particles, uniform random with
     probability 1/2, else the clustered generator with 8 Plummer spheres
-    scaled to N_b. m = 1/N_b, u = 1, v = 0."""
+    scaled to N_b. m = 1/N_b, u = 1, v = 0.
+
+    A clustered box needs at least `min_clustered` particles: below that its
+    uniform 30% background is too sparse for 48 neighbours within L/3 (the
+    largest smoothing length a periodic box of three cells per axis admits),
+    so such boxes are uniform."""
     rng = np.random.default_rng(seed)
     sizes = np.round(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_boxes))).astype(np.int64)
     kinds = rng.random(n_boxes) < 0.5
     parts = []
     for b in range(n_boxes):
         s = int(rng.integers(0, 2**31 - 1))
-        if kinds[b]:
+        if kinds[b] or sizes[b] < min_clustered:
             p = uniform(int(sizes[b]), seed=s)
         else:
             p = clustered(int(sizes[b]), n_spheres=8, seed=s)
