@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["plain", "batched"], default="plain")
+    ap.add_argument("--mode", choices=["plain", "batched"], default="batched")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other interaction form for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sod", choices=["sod", "uniform", "clustered",
@@ -353,6 +355,35 @@ def run_ours(args, d: Dist):
     e2e_val = (d.reduce(float(e2e_inter), "SUM") / (e2e_ms_max / 1000.0)
                if e2e_ms_max > 0 else None)
 
+    # the other interaction form, same workload, same protocol (comparison)
+    other = None
+    if not args.no_compare:
+        omode = sph.SPH_MODE_PLAIN if mode == sph.SPH_MODE_BATCHED else sph.SPH_MODE_BATCHED
+        oc = sph.Context(mode=omode, profile=True, device=dev)
+        oc.load(p)
+        oc.density()
+        oc.force()
+        for _ in range(args.warmup):
+            oc.step(dt, 1)
+        torch.cuda.synchronize(dev)
+        o0 = oc.stats()
+        oev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            oev[k][0].record(stream)
+            oc.step(dt, 1)
+            oev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        o1 = oc.stats()
+        oms = sum(a.elapsed_time(b) for a, b in oev)
+        ointer = (o1["total_density_interactions"] - o0["total_density_interactions"] +
+                  o1["total_force_interactions"] - o0["total_force_interactions"])
+        other = {"mode": "plain" if omode == sph.SPH_MODE_PLAIN else "batched",
+                 "value": ointer / (oms / 1000.0), "ms_per_step": oms / args.steps,
+                 "interactions_per_step": ointer / args.steps}
+        oc.close()
+
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -381,6 +412,7 @@ def run_ours(args, d: Dist):
                     "step": "H2D inputs, sph_init, sph_density, sph_force, sph_step(dt, 1), "
                             "D2H x v u h"},
             "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
+            "other_form": other,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
