@@ -36,6 +36,7 @@ METRIC = "SPH neighbour interactions/sec (density+force) on 1 GB300; % FP32 roof
 UNIT = "interactions/s"
 FLOPS_DENSITY = 29   # per density interaction (FFMA = 2)
 FLOPS_FORCE = 44     # per force interaction
+SORT_BYTES_PER_PARTICLE = 16 + 13 * (4 + 4)  # pair-axis sorts: pm read, 13 keys + indices
 SOD_DT = 7e-4        # 0.1 * min(h / c) of the initial state, rounded down
 
 
@@ -46,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["plain", "batched"], default="batched")
+    ap.add_argument("--no-pair-sort", action="store_true",
+                    help="per-pass form without the pair-axis sorts (whole source leaves)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other interaction form for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -169,39 +172,58 @@ def fp32_peak_tflops(sm_count: int) -> tuple[float, str]:
                   f"(MEASURED_PEAKS.json sm_max_mhz)")
 
 
-def kernel_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu capture, only while the
-    kernel source it was taken on is unchanged."""
+def hbm_peak_gbs() -> tuple[float, str]:
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_traffic(kernel: str, mode: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from a committed ncu capture of this kernel in this form, only while the
+    source files it was taken on are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel)
+        rec = json.load(open(path)).get(f"{kernel}_{mode}")
     except (OSError, ValueError):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1606_02738_gb300", "csrc", "interact.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h:
+    if rec.get("source_sha") != source_sha(rec.get("sources", [])):
         return None
     return rec.get("bytes_per_launch")
 
 
+def source_sha(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1606_02738_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 # ------------------------------------------------------------ CPU oracle
 
-def cpu_baseline(p, budget_s: float = 30.0) -> dict:
-    """The FP64 oracle, as it stands, on one density + force evaluation of
-    the workload (all particles), on this host's cores."""
+def cpu_baseline(p, min_s: float = 10.0, max_reps: int = 20) -> dict:
+    """The FP64 oracle, as it stands, on h-iterated density + force
+    evaluations of the workload (all particles, from the generator's h),
+    repeated until at least `min_s` seconds of CPU work, on this host's
+    cores."""
     import oracle
     oracle.build()
-    s = oracle.State.from_particles(p)
-    t0 = time.perf_counter()
-    oracle.compute_density(s)
-    oracle.compute_force(s)
-    dt = time.perf_counter() - t0
-    inter = int(s.n_dens.sum() + s.n_force.sum())
+    inter, dt, reps = 0, 0.0, 0
+    while reps < max_reps and (dt < min_s or reps == 0):
+        s = oracle.State.from_particles(p)
+        t0 = time.perf_counter()
+        oracle.compute_density(s)
+        oracle.compute_force(s)
+        dt += time.perf_counter() - t0
+        inter += int(s.n_dens.sum() + s.n_force.sum())
+        reps += 1
     return {"value": inter / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one h-iterated density + force evaluation of all {p.n} particles of "
-                      f"the initial state ({inter} interactions, {dt:.2f} s)",
+            "sample": f"{reps} h-iterated density + force evaluations of all {p.n} particles "
+                      f"of the initial state ({inter} interactions, {dt:.2f} s)",
             "seconds": dt}
 
 
@@ -261,7 +283,7 @@ def run_ours(args, d: Dist):
     p, dt, wname = workload(args.workload)
     mode = sph.SPH_MODE_BATCHED if args.mode == "batched" else sph.SPH_MODE_PLAIN
     stream = torch.cuda.current_stream(dev)
-    ctx = sph.Context(mode=mode, profile=True, device=dev)
+    ctx = sph.Context(mode=mode, profile=True, pair_sort=not args.no_pair_sort, device=dev)
     ctx.load(p)
     ctx.density()
     ctx.force()
@@ -310,13 +332,24 @@ def run_ours(args, d: Dist):
                       "flops_per_launch": flops * ikey / n}
     dom = max(kern, key=lambda k: kern[k]["share_of_step"])
     roof = {"bound": "alu", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
-            "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom),
+            "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom, args.mode),
             "kernel": dom, "peak_source": peak_src,
             "flops_per_interaction": {"density": FLOPS_DENSITY, "force": FLOPS_FORCE},
             "kernels": kern}
+    # the pair-axis sort kernel: HBM-bound, algorithmic bytes per particle =
+    # one float4 read + 13 (key, index) pairs written
+    t_sort = s1["t_sort_ms"] - s0["t_sort_ms"]
+    n_sort = s1["sort_launches"] - s0["sort_launches"]
+    if t_sort > 0 and n_sort > 0:
+        gbs = SORT_BYTES_PER_PARTICLE * p.n * n_sort / (t_sort / 1000.0) / 1e9
+        hbm = hbm_peak_gbs()
+        roof["axis_sort"] = {"bound": "hbm", "achieved": gbs, "peak": hbm[0], "unit": "GB/s",
+                             "frac": gbs / hbm[0], "peak_source": hbm[1],
+                             "bytes_per_particle": SORT_BYTES_PER_PARTICLE,
+                             "ms_per_launch": t_sort / n_sort, "launches": n_sort}
     stages = {k: (s1[k] - s0[k]) / args.steps for k in
-              ("t_grid_ms", "t_lists_ms", "t_density_ms", "t_ghost_ms", "t_force_ms",
-               "t_integrate_ms")}
+              ("t_grid_ms", "t_sort_ms", "t_lists_ms", "t_density_ms", "t_ghost_ms",
+               "t_force_ms", "t_integrate_ms")}
 
     # end to end through the C ABI with host buffers: H2D of the inputs from
     # pinned memory, init + density + force + one KDK step, D2H of x, v, u, h
@@ -359,7 +392,7 @@ def run_ours(args, d: Dist):
     other = None
     if not args.no_compare:
         omode = sph.SPH_MODE_PLAIN if mode == sph.SPH_MODE_BATCHED else sph.SPH_MODE_BATCHED
-        oc = sph.Context(mode=omode, profile=True, device=dev)
+        oc = sph.Context(mode=omode, profile=True, pair_sort=not args.no_pair_sort, device=dev)
         oc.load(p)
         oc.density()
         oc.force()
@@ -402,7 +435,11 @@ def run_ours(args, d: Dist):
                        "interactions_per_step": inter / args.steps,
                        "density_passes_last_step": s1["density_passes"],
                        "batched_fallbacks_last_step": s1["batched_fallbacks"],
+                       "fallback_causes_last_step": s1["fallback_causes"],
                        "stage_max": [s1["stage_max_density"], s1["stage_max_force"]],
+                       "direct_warps_last_step": [s1["direct_list_warps"],
+                                                  s1["direct_stage_warps"]],
+                       "pair_sort": not args.no_pair_sort,
                        "leaves": s1["n_leaves"]},
             "roofline": roof,
             "stage_ms_per_step": stages,

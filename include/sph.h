@@ -69,7 +69,8 @@ extern "C" {
 
 /* ---- interaction-kernel forms ---- */
 #define SPH_MODE_PLAIN 0   /* one launch per density pass, host-driven h iteration */
-#define SPH_MODE_BATCHED 1 /* persistent work-queue kernels, in-kernel h iteration, CUDA graph */
+#define SPH_MODE_BATCHED 1 /* one block per group of <= 32 particles, h iteration inside the
+                              kernel; particles it cannot finish go to the per-pass form */
 
 /* ---- precision ---- */
 #define SPH_PREC_FP32 0  /* FP32 pair arithmetic and accumulation */
@@ -86,7 +87,12 @@ typedef struct {
   int precision;   /* SPH_PREC_* */
   int mode;        /* SPH_MODE_* */
   int profile;     /* 1: time each stage with CUDA events on the context stream */
-  int reserved[3]; /* zero */
+  int pair_sort;   /* 1: sort each leaf's particles along the 13 pair axes (Section 3.1)
+                      before the first per-pass kernel after a regrid, and let the
+                      per-pass kernels visit only the source particles whose key along a
+                      pair's axis is within reach; 0: visit whole source leaves (same
+                      results, more pairs tested). The batched kernels do not use them. */
+  int reserved[2]; /* zero */
 } sph_params;
 
 typedef struct {
@@ -122,10 +128,24 @@ typedef struct {
   double t_ghost_ms;          /* h update / finalisation kernel */
   double t_force_ms;          /* force interaction kernel only */
   double t_integrate_ms;      /* kick / drift kernels */
+  double t_sort_ms;           /* pair-axis sorts of every leaf (pair_sort = 1) */
+  /* Last sph_density + sph_force, batched form: warps of a group whose
+   * per-lane neighbour lists overflowed and that read their pre-filtered
+   * candidates directly, and warps whose candidates overflowed and that read
+   * the group's whole stage (same results, more pairs tested). */
+  int32_t direct_list_warps;
+  int32_t direct_stage_warps;
+  /* Particles of the last sph_density + sph_force that the batched kernels
+   * left to the per-pass form, by cause: [0] density group stage or task
+   * slots overflowed, [1] a density h grew beyond the staged radius, [2] an
+   * h not converged in max_iter passes, [3] force group stage or task slots
+   * overflowed. */
+  int32_t fallback_causes[4];
+  int64_t sort_launches;      /* pair-axis sort launches (cumulative since sph_create) */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,
- * n_split = 64, FP32, batched mode. */
+ * n_split = 64, FP32, batched mode, pair sorts on, profiling off. */
 void sph_default_params(sph_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a
@@ -177,6 +197,18 @@ int sph_step(sph_ctx *ctx, double dt, int n_steps);
  * at the field). Asynchronous. Errors: SPH_EINVAL (unknown field / null),
  * SPH_ESTATE (field not computed yet). */
 int sph_get(sph_ctx *ctx, int field, void *dev_out);
+
+/* Pair-axis sort of the current grid along direction `axis` (0..12; the
+ * integer offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1)
+ * (0,1,1) (0,1,-1) (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1), normalised), Section
+ * 3.1: the particles of every octree leaf ranked by x . e_axis (ties by
+ * position in the leaf). Writes two int32 device arrays of N entries, one per
+ * slot of the library's leaf-ordered store: `leaf_out[s]` = the leaf holding
+ * slot s (leaves occupy consecutive slots), `order_out[s]` = the caller
+ * index of the particle of rank s - (first slot of that leaf). Asynchronous.
+ * Errors: SPH_EINVAL (axis out of range, null output), SPH_ESTATE (no
+ * particles loaded, or pair_sort = 0). */
+int sph_get_pair_order(sph_ctx *ctx, int axis, int32_t *order_out, int32_t *leaf_out);
 
 /* Counters of the last density/force calls (synchronises the stream). */
 int sph_stats(sph_ctx *ctx, sph_stats_t *out);

@@ -551,6 +551,39 @@ __device__ __forceinline__ float slice_sum(float v) {
   return v;
 }
 
+// One lane's density sums (Eq. rho and the h-derivative terms) over its
+// share of the candidates: q = r / h_i for r^2 < h2.
+template <bool KAHAN>
+struct DensAcc {
+  float sw = 0.f, sdw = 0.f, smw = 0.f, smdh = 0.f;
+  float cw = 0.f, cdw = 0.f, cmw = 0.f, cmdh = 0.f;
+  int c = 0;
+  __device__ __forceinline__ void add(float4 q, float px, float py, float pz, float h2,
+                                      float hinv) {
+    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < h2) {
+      const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+      const float qq = r * hinv;
+      float w, dw;
+      w_and_dw(qq, w, dw);
+      const float qdw = qq * dw;
+      if (KAHAN) {
+        add_comp(sw, cw, w);
+        add_comp(sdw, cdw, qdw);
+        add_comp(smw, cmw, q.w * w);
+        add_comp(smdh, cmdh, q.w * fmaf(3.f, w, qdw));
+      } else {
+        sw += w;
+        sdw += qdw;
+        smw = fmaf(q.w, w, smw);
+        smdh = fmaf(q.w, fmaf(3.f, w, qdw), smdh);
+      }
+      ++c;
+    }
+  }
+};
+
 template <bool KAHAN>
 __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -560,7 +593,8 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0;
+  int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
+  int why[3] = {0, 0, 0};  // fallback causes: stage/task overflow, h beyond the stage, passes
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
@@ -575,7 +609,7 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
     stage_max = max(stage_max, sr.total);
     if (sr.total > kStageD || nt > a.tcap) {  // block-uniform: the group goes to the per-pass form
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback;
+        ++fallback, ++why[0];
       continue;
     }
     const int nst = sr.total;
@@ -603,11 +637,15 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
     sub_box(has, px, py, pz, blo, bhi);
 
     bool failed = false, fin = !has, need_list = has, need_filter = true;
+    // 0: per-lane lists; 1: a lane's list outgrew kLane, the warp reads its
+    // candidates directly; 2: the candidates outgrew kCandD, the warp reads
+    // the whole stage (slower, same sums)
+    int mode = 0;
     int ncand = 0, cnt = 0, passes = 0, ngb = 0;
     float rsub = 0.f, rl = 0.f;
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; pass < a.max_iter; ++pass) {
-      if (__any_sync(0xffffffffu, need_filter)) {
+      if (mode < 2 && __any_sync(0xffffffffu, need_filter)) {
         // sub-cluster radius: its largest h x the stage skin, capped by Rg
         float hm = has && !fin ? (float)it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
@@ -615,12 +653,9 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
         ncand = filter_stage<false>(S.stage, nullptr, nst, blo, bhi, rsub, cand, kCandD, lane);
         need_filter = false;
         need_list = !fin;
-        if (__any_sync(0xffffffffu, ncand > kCandD)) {
-          failed = true;
-          break;
-        }
+        if (ncand > kCandD) mode = 2;  // ncand is warp-uniform
       }
-      if (__any_sync(0xffffffffu, need_list)) {
+      if (mode == 0 && __any_sync(0xffffffffu, need_list)) {
         float rl2 = -1.f;
         if (need_list) {
           rl = fminf((float)it.h * a.skin_list, rsub);
@@ -640,49 +675,28 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
           }
         }
         need_list = false;
-        if (__any_sync(0xffffffffu, cnt > kLane)) {
-          failed = true;
-          break;
-        }
+        if (__any_sync(0xffffffffu, cnt > kLane)) mode = 1;
         __syncwarp();
       }
       // partial sums over this lane's slice at the current h
       const float hf = (float)it.h;
       const float h2 = fin ? -1.f : hf * hf;
       const float hinv = 1.f / hf;
-      float sw = 0.f, sdw = 0.f, smw = 0.f, smdh = 0.f;
-      float cw = 0.f, cdw = 0.f, cmw = 0.f, cmdh = 0.f;
-      int c = 0;
-      const int tmax = warp_max_int(fin ? 0 : cnt);
-      for (int t = 0; t < tmax; ++t) {
-        if (t < cnt && !fin) {
-          const float4 q = S.stage[list[t * 32 + lane]];
-          const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < h2) {
-            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-            const float qq = r * hinv;
-            float w, dw;
-            w_and_dw(qq, w, dw);
-            const float qdw = qq * dw;
-            if (KAHAN) {
-              add_comp(sw, cw, w);
-              add_comp(sdw, cdw, qdw);
-              add_comp(smw, cmw, q.w * w);
-              add_comp(smdh, cmdh, q.w * fmaf(3.f, w, qdw));
-            } else {
-              sw += w;
-              sdw += qdw;
-              smw = fmaf(q.w, w, smw);
-              smdh = fmaf(q.w, fmaf(3.f, w, qdw), smdh);
-            }
-            ++c;
-          }
-        }
+      DensAcc<KAHAN> acc;
+      if (mode == 0) {
+        const int tmax = warp_max_int(fin ? 0 : cnt);
+        for (int t = 0; t < tmax; ++t)
+          if (t < cnt && !fin) acc.add(S.stage[list[t * 32 + lane]], px, py, pz, h2, hinv);
+        if (!fin) ntest += cnt;
+      } else {
+        const int nsrc = mode == 1 ? ncand : nst;
+        for (int t = slice; t < nsrc; t += kSlice)
+          acc.add(S.stage[mode == 1 ? (int)cand[t] : t], px, py, pz, h2, hinv);
+        if (!fin) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
       }
-      if (!fin) ntest += cnt;
-      const float4 tot = make_float4(slice_sum(sw), slice_sum(sdw), slice_sum(smw), slice_sum(smdh));
-      int ctot = c;
+      const float4 tot = make_float4(slice_sum(acc.sw), slice_sum(acc.sdw), slice_sum(acc.smw),
+                                     slice_sum(acc.smdh));
+      int ctot = acc.c;
       ctot += __shfl_xor_sync(0xffffffffu, ctot, 1);
       ctot += __shfl_xor_sync(0xffffffffu, ctot, 2);
       if (!fin) {
@@ -706,8 +720,12 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
       }
       if (__all_sync(0xffffffffu, fin)) break;
     }
+    if (lane == 0 && mode) ++n_direct[mode - 1];
     if (failed || !__all_sync(0xffffffffu, fin)) {
-      if (has && slice == 0) ++fallback;  // left to the per-pass form
+      if (has && slice == 0) {  // left to the per-pass form
+        ++fallback;
+        ++why[failed ? 1 : 2];
+      }
       continue;
     }
     if (has && slice == 0) {
@@ -743,6 +761,12 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
     if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
     if (st_bits) atomicOr(&a.ctr->status, st_bits);
     atomicMax(&a.ctr->stage_max[0], stage_max);
+    if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
+    if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    const int w = (int)warp_sum((unsigned long long)why[k]);
+    if (lane == 0 && w) atomicAdd(&a.ctr->why[k], w);
   }
 }
 
@@ -766,6 +790,34 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   note_launch();
 }
 
+// One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
+// particles. hi2 < 0: the entry is a listed neighbour (accepted); otherwise
+// the pair is tested, r > 0 and r^2 < max(h_i^2, h_j^2).
+struct ForceAcc {
+  float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+  int c = 0;
+  __device__ __forceinline__ void add(const ForceSmem &S, int k, const float4 *vu, float px,
+                                      float py, float pz, float4 fi, float4 vi, float hi2) {
+    const float4 q = S.sq[k];
+    const float2 f = S.sf[k];
+    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (hi2 >= 0.f && !(r2 > 0.f && r2 < fmaxf(hi2, f.y))) return;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float ti = fi.z * dw_only(r * fi.y);         // A_i dW/dr(r, h_i)
+    const float tj = f.x * dw_only(r * rsqrtf(f.y));   // A_j dW/dr(r, h_j)
+    const float fac = q.w * (ti + tj) * rinv;
+    const float4 vj = vu[S.sj[k]];
+    const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+    ax = fmaf(-fac, dx, ax);
+    ay = fmaf(-fac, dy, ay);
+    az = fmaf(-fac, dz, az);
+    du = fmaf(q.w * ti * rinv, dvdx, du);
+    ++c;
+  }
+};
+
 __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
@@ -774,7 +826,8 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int fallback = 0, stage_max = 0;
+  int fallback = 0, stage_max = 0, n_direct[2] = {0, 0};
+  int why0 = 0;  // fallbacks for stage or task overflow
 
   for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
     const Group G = a.groups[g];
@@ -785,7 +838,7 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
     stage_max = max(stage_max, sr.total);
     if (sr.total > kStageF || nt > a.tcap) {  // block-uniform
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback;
+        ++fallback, ++why0;
       continue;
     }
     const int tloc = warp * kSub + (lane >> 2);
@@ -808,52 +861,45 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
     const int ncand = filter_stage<true>(S.sq, S.sf, sr.total, blo, bhi, hm, cand, kCandF, lane);
-    if (__any_sync(0xffffffffu, ncand > kCandF)) {
-      if (has && slice == 0) ++fallback;
-      continue;
-    }
+    // 0: per-lane lists; 1: a list outgrew kLane, the warp reads its
+    // candidates directly; 2: the candidates outgrew kCandF, it reads the
+    // whole stage (ncand is warp-uniform)
+    int mode = ncand > kCandF ? 2 : 0;
     const float hi2 = has ? fi.w : -1.f;
     int cnt = 0;
+    if (mode == 0) {
 #pragma unroll 4
-    for (int t = slice; t < ncand; t += kSlice) {
-      const int k = cand[t];
-      const float4 q = S.sq[k];
-      const float hj2 = S.sf[k].y;
-      const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-        if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
-        ++cnt;
-      }
-    }
-    if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
-    if (__any_sync(0xffffffffu, cnt > kLane)) {
-      if (has && slice == 0) ++fallback;
-      continue;
-    }
-    __syncwarp();
-    float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
-    const int tmax = warp_max_int(has ? cnt : 0);
-    for (int t = 0; t < tmax; ++t) {
-      if (t < cnt) {
-        const int k = list[t * 32 + lane];
+      for (int t = slice; t < ncand; t += kSlice) {
+        const int k = cand[t];
         const float4 q = S.sq[k];
-        const float2 f = S.sf[k];
+        const float hj2 = S.sf[k].y;
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
-        const float tj = f.x * dw_only(r * rsqrtf(f.y));  // A_j dW/dr(r, h_j)
-        const float fac = q.w * (ti + tj) * rinv;
-        const float4 vj = a.vu[S.sj[k]];
-        const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-        ax = fmaf(-fac, dx, ax);
-        ay = fmaf(-fac, dy, ay);
-        az = fmaf(-fac, dz, az);
-        du = fmaf(q.w * ti * rinv, dvdx, du);
+        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+          if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
+          ++cnt;
+        }
       }
+      if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
+      if (__any_sync(0xffffffffu, cnt > kLane)) mode = 1;
+      __syncwarp();
     }
+    ForceAcc acc;
+    if (mode == 0) {
+      const int tmax = warp_max_int(has ? cnt : 0);
+      for (int t = 0; t < tmax; ++t)
+        if (t < cnt) acc.add(S, list[t * 32 + lane], a.vu, px, py, pz, fi, vi, -1.f);
+      if (has) ntest += cnt;
+    } else {
+      const int nsrc = mode == 1 ? ncand : sr.total;
+      if (has)
+        for (int t = slice; t < nsrc; t += kSlice)
+          acc.add(S, mode == 1 ? (int)cand[t] : t, a.vu, px, py, pz, fi, vi, hi2);
+      if (has) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
+    }
+    if (lane == 0 && mode) ++n_direct[mode - 1];
+    cnt = acc.c;
+    float ax = acc.ax, ay = acc.ay, az = acc.az, du = acc.du;
     ax = slice_sum(ax);
     ay = slice_sum(ay);
     az = slice_sum(az);
@@ -861,7 +907,6 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
     int ctot = cnt;
     ctot += __shfl_xor_sync(0xffffffffu, ctot, 1);
     ctot += __shfl_xor_sync(0xffffffffu, ctot, 2);
-    if (has) ntest += cnt;
     if (has && slice == 0) {
       a.acc[i] = make_float4(ax, ay, az, du);
       a.nforce[i] = ctot;
@@ -880,7 +925,11 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
       atomicAdd(&a.ctr->fallback, fallback);
     }
     atomicMax(&a.ctr->stage_max[1], stage_max);
+    if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
+    if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
+  why0 = (int)warp_sum((unsigned long long)why0);
+  if (lane == 0 && why0) atomicAdd(&a.ctr->why[3], why0);
 }
 
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {

@@ -19,7 +19,9 @@
 //
 // Layout: one warp per target leaf; the i particles sit in lanes, the j
 // particles of each source leaf are staged in shared memory (shifted into the
-// target leaf's frame) and read as warp-wide broadcasts.
+// target leaf's frame) and read as warp-wide broadcasts. For a pair task only
+// the source particles whose key along the pair's sort axis lies within reach
+// of the warp's targets are staged (pair-axis sorts, Section 3.1).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +43,33 @@ __device__ __forceinline__ void add_comp(float &s, float &c, float v) {
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Pair-axis pruning of one task for the warp's 32 targets: the rank range
+// [r0, r1) of the source leaf's particles, sorted along the direction nearest
+// the task's shift, whose keys lie within reach R of some active target's key
+// (|d_i - d_j| <= r_ij, so no neighbour is cut). `ix` maps a rank to the
+// leaf-local index; it is null (whole leaf, unsorted) for the self task or
+// when no sorts are given.
+__device__ __forceinline__ void source_range(const float *skey, const int *sidx, int n,
+                                             const Task &tk, int T, const Leaf &LS, bool act,
+                                             float4 pi, float R, int &r0, int &r1,
+                                             const int *&ix) {
+  r0 = 0;
+  r1 = LS.count;
+  ix = nullptr;
+  if (!skey || (tk.src == T && tk.sx == 0.f && tk.sy == 0.f && tk.sz == 0.f)) return;
+  const int k = warp_best_axis(tk.sx, tk.sy, tk.sz);
+  const float3 e = axis_vec(k);
+  const float sd = fmaf(tk.sx, e.x, fmaf(tk.sy, e.y, tk.sz * e.z));
+  float lo, hi;
+  if (!warp_key_window(act, axis_key(pi, e), R, sd, lo, hi)) {
+    r1 = 0;  // no active target in the warp
+    return;
+  }
+  const size_t base = (size_t)k * n + LS.start;
+  warp_key_range(skey + base, LS.count, lo, hi, r0, r1);
+  ix = sidx + base;
 }
 
 // ---------------------------------------------------------------- density
@@ -74,11 +103,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_density(DensArgs a) {
       for (int e = e0; e < e1; ++e) {
         const Task tk = a.tasks[e];
         const Leaf LS = a.leaves[tk.src];
-        for (int jb = 0; jb < LS.count; jb += kStage) {
-          const int nj = min(kStage, LS.count - jb);
+        int r0, r1;
+        const int *ix;
+        source_range(a.skey, a.sidx, a.n, tk, T, LS, act, pi, hi, r0, r1, ix);
+        for (int jb = r0; jb < r1; jb += kStage) {
+          const int nj = min(kStage, r1 - jb);
           __syncwarp();
           for (int k = lane; k < nj; k += 32) {
-            float4 q = a.pm[LS.start + jb + k];
+            float4 q = a.pm[LS.start + (ix ? ix[jb + k] : jb + k)];
             q.x += tk.sx;
             q.y += tk.sy;
             q.z += tk.sz;
@@ -236,11 +268,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(ForceArgs a) {
       for (int e = e0; e < e1; ++e) {
         const Task tk = a.tasks[e];
         const Leaf LS = a.leaves[tk.src];
-        for (int jb = 0; jb < LS.count; jb += kStage) {
-          const int nj = min(kStage, LS.count - jb);
+        int r0, r1;
+        const int *ix;
+        const float reach = a.skey ? fmaxf(fi.x, a.nodes[LS.node].hmax) : 0.f;
+        source_range(a.skey, a.sidx, a.n, tk, T, LS, has, pi, reach, r0, r1, ix);
+        for (int jb = r0; jb < r1; jb += kStage) {
+          const int nj = min(kStage, r1 - jb);
           __syncwarp();
           for (int k = lane; k < nj; k += 32) {
-            const int j = LS.start + jb + k;
+            const int j = LS.start + (ix ? ix[jb + k] : jb + k);
             float4 q = a.pm[j];
             q.x += tk.sx;
             q.y += tk.sy;

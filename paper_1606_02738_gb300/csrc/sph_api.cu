@@ -55,6 +55,8 @@ struct sph_ctx {
   StoreArrays st{}, st2{};
   float *hf = nullptr;
   float4 *pm = nullptr, *sums = nullptr, *fi = nullptr;
+  float *skey = nullptr;  // pair-axis sorts: [kAxes][n] keys, rank order per leaf
+  int *sidx = nullptr;    // [kAxes][n] leaf-local index of each rank
   int *cnt = nullptr, *niter = nullptr, *nngb = nullptr, *nforce = nullptr, *leaf_of = nullptr;
   unsigned char *done = nullptr, *fdone = nullptr;
   float *rho = nullptr, *omega = nullptr, *P = nullptr, *fprev = nullptr;
@@ -79,14 +81,15 @@ struct sph_ctx {
   DevCounters *ctr_h = nullptr;  // pinned host mirror
 
   bool loaded = false, grid_valid = false, density_valid = false, force_valid = false;
+  bool sorts_valid = false;  // pair-axis sorts match the current grid
   int last_passes = 0, last_rebuilds = 0;
   // cumulative counters and stage timers
-  long long launches = 0, dens_launches = 0, force_launches = 0;
+  long long launches = 0, dens_launches = 0, force_launches = 0, sort_launches = 0;
   unsigned long long total_dens_inter = 0, total_force_inter = 0;
   bool force_pending = false;  // force counters on the device not yet added to the totals
-  cudaEvent_t ev[6][2] = {};
-  bool ev_pending[6] = {};
-  double t_ms[6] = {};
+  cudaEvent_t ev[7][2] = {};
+  bool ev_pending[7] = {};
+  double t_ms[7] = {};
 };
 
 namespace sph {
@@ -95,7 +98,7 @@ thread_local long long *g_launch_count = nullptr;
 
 namespace {
 
-enum Stage { kGrid = 0, kLists, kDens, kGhost, kForce, kInteg };
+enum Stage { kGrid = 0, kLists, kDens, kGhost, kForce, kInteg, kSort, kNStages };
 
 // Points the launch counter at this context for the duration of an API call.
 struct LaunchScope {
@@ -115,7 +118,7 @@ void toc(sph_ctx *c, Stage s) {
 // Add the elapsed time of every bracket whose closing event was recorded.
 void collect_timers(sph_ctx *c) {
   if (!c->p.profile) return;
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < kNStages; ++s) {
     if (!c->ev_pending[s]) continue;
     if (cudaEventSynchronize(c->ev[s][1]) != cudaSuccess) continue;
     float ms = 0.f;
@@ -206,6 +209,8 @@ FixedLayout fixed_layout(int64_t n, int nb) {
   }
   add(N * sizeof(float));          // hf
   add(N * sizeof(float4));         // pm
+  add((size_t)kAxes * N * sizeof(float));  // skey
+  add((size_t)kAxes * N * sizeof(int));    // sidx
   add(N * sizeof(float4));         // sums
   add(N * sizeof(float4));         // fi
   for (int k = 0; k < 5; ++k) add(N * sizeof(int));  // cnt niter nngb nforce leaf_of
@@ -267,6 +272,8 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   }
   take(c->hf);
   take(c->pm);
+  take(c->skey);
+  take(c->sidx);
   take(c->sums);
   take(c->fi);
   take(c->cnt);
@@ -512,7 +519,22 @@ int build_grid(sph_ctx *c, bool from_caller, const float *cv, const float *cm, c
   tic(c, kGrid);
   int rc = build_grid_inner(c, from_caller, cv, cm, cu, ch);
   toc(c, kGrid);
+  c->sorts_valid = false;
   return rc;
+}
+
+// A3: every leaf's particles sorted along the 13 pair axes, once per grid,
+// before the first per-pass (leaf-pair task) kernel that prunes with them.
+// The batched kernels do not read them, so a step they finish alone sorts
+// nothing.
+void ensure_sorts(sph_ctx *c) {
+  if (!c->p.pair_sort || c->sorts_valid) return;
+  tic(c, kSort);
+  AxisSortArgs sa{c->n_leaves, as<Leaf>(c->leaves), c->pm, c->n, c->skey, c->sidx};
+  launch_axis_sort(sa, c->stream);
+  toc(c, kSort);
+  ++c->sort_launches;
+  c->sorts_valid = true;
 }
 
 GeomArgs geom_args(sph_ctx *c) {
@@ -727,6 +749,10 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
     da.cnt = c->cnt;
     da.ctr = c->ctr;
     da.kahan = c->p.precision == SPH_PREC_KAHAN;
+    da.skey = c->p.pair_sort ? c->skey : nullptr;
+    da.sidx = c->sidx;
+    da.n = c->n;
+    ensure_sorts(c);
     tic(c, kDens);
     launch_density(da, c->stream);
     toc(c, kDens);
@@ -875,6 +901,11 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   fa.nforce = c->nforce;
   fa.ctr = c->ctr;
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
+  fa.nodes = as<Node>(c->nodes);
+  fa.skey = c->p.pair_sort ? c->skey : nullptr;
+  fa.sidx = c->sidx;
+  fa.n = c->n;
+  ensure_sorts(c);
   tic(c, kForce);
   launch_force(fa, c->stream);
   toc(c, kForce);
@@ -898,7 +929,8 @@ void sph_default_params(sph_params *p) {
   p->max_iter = 30;
   p->n_split = 64;
   p->precision = SPH_PREC_FP32;
-  p->mode = SPH_MODE_PLAIN;
+  p->mode = SPH_MODE_BATCHED;
+  p->pair_sort = 1;
 }
 
 int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
@@ -910,7 +942,8 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
   if (!(q.gamma > 1.0) || !(q.n_ngb > 32.0 / 3.0) || !(q.h_tol > 0.0) || q.max_iter < 1 ||
       q.n_split < 8 || q.n_split > 256 ||
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
-      (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED))
+      (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
+      (q.pair_sort != 0 && q.pair_sort != 1))
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;
@@ -1059,6 +1092,20 @@ int sph_get(sph_ctx *c, int field, void *dev_out) {
   return sync_check(c);
 }
 
+int sph_get_pair_order(sph_ctx *c, int axis, int32_t *order_out, int32_t *leaf_out) {
+  if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
+  c->err.clear();
+  if (axis < 0 || axis >= kAxes || !order_out || !leaf_out)
+    return fail(c, SPH_EINVAL, "axis %d out of range or null output", axis);
+  if (!c->loaded || !c->grid_valid) return fail(c, SPH_ESTATE, "no particles loaded");
+  if (!c->p.pair_sort) return fail(c, SPH_ESTATE, "pair sorts are off (pair_sort = 0)");
+  ensure_sorts(c);
+  launch_get_pair_order(as<Leaf>(c->leaves), c->leaf_of, c->sidx, c->st.orig, c->n, axis,
+                        order_out, leaf_out, c->stream);
+  return sync_check(c);
+}
+
 int sph_stats(sph_ctx *c, sph_stats_t *out) {
   if (!c || !out) return SPH_EINVAL;
   LaunchScope ls(c);
@@ -1091,6 +1138,11 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->t_ghost_ms = c->t_ms[kGhost];
   out->t_force_ms = c->t_ms[kForce];
   out->t_integrate_ms = c->t_ms[kInteg];
+  out->t_sort_ms = c->t_ms[kSort];
+  out->direct_list_warps = c->ctr_h->direct[0];
+  out->direct_stage_warps = c->ctr_h->direct[1];
+  for (int k = 0; k < 4; ++k) out->fallback_causes[k] = c->ctr_h->why[k];
+  out->sort_launches = c->sort_launches;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
   double hmin = 0, hmax = 0;

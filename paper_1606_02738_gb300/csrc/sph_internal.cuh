@@ -84,6 +84,11 @@ struct DevCounters {
   int n_frontier;
   int fallback;                       // particles the batched kernels left to the per-pass form
   int stage_max[2];                   // largest group stage (density, force) of the batched form
+  int direct[2];                      // batched warp-groups that read their candidates
+                                      // directly (a list overflowed) / the whole stage
+  int why[4];                         // batched fallbacks: density stage or task overflow,
+                                      // density h beyond the stage, density passes, force
+                                      // stage or task overflow
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
@@ -180,6 +185,82 @@ __device__ __forceinline__ bool finalise_density(double h, float4 s, double u, d
   return rho > 0.f && omega > 0.f && u >= 0.0;
 }
 
+// ---- pair-axis sorts (Section 3.1: particles are sorted along the axis of
+// each pair of neighbouring cells before the density tasks run) ----
+constexpr int kAxes = 13;
+// Integer offsets to 13 of the 26 neighbouring cells; the other 13 are their
+// negatives. Each has its first non-zero component positive.
+static __constant__ signed char kAxisDir[kAxes][3] = {
+    {1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},   {1, -1, 0},  {1, 0, 1},  {1, 0, -1},
+    {0, 1, 1},  {0, 1, -1}, {1, 1, 1},  {1, 1, -1},  {1, -1, 1},  {1, -1, -1}};
+
+// Unit vector of direction k.
+__device__ __forceinline__ float3 axis_vec(int k) {
+  const float a = kAxisDir[k][0], b = kAxisDir[k][1], c = kAxisDir[k][2];
+  const int nz = (a != 0.f) + (b != 0.f) + (c != 0.f);
+  const float s = nz == 1 ? 1.f : (nz == 2 ? 0.70710678118654752f : 0.57735026918962576f);
+  return make_float3(a * s, b * s, c * s);
+}
+
+__device__ __forceinline__ float axis_key(float4 p, float3 e) {
+  return fmaf(p.x, e.x, fmaf(p.y, e.y, p.z * e.z));
+}
+
+// Direction (of the 13) most nearly parallel to the offset d, with |d . e|.
+// Computed by a whole warp (lanes 0..12 score one direction each); every lane
+// receives the winner. Ties go to the lowest index.
+__device__ __forceinline__ int warp_best_axis(float dx, float dy, float dz) {
+  const int lane = threadIdx.x & 31;
+  float v = -1.f;
+  if (lane < kAxes) {
+    const float3 e = axis_vec(lane);
+    v = fabsf(fmaf(dx, e.x, fmaf(dy, e.y, dz * e.z)));
+  }
+  float m = v;
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const unsigned hit = __ballot_sync(0xffffffffu, v == m);
+  return __ffs(hit) - 1;
+}
+
+// Window [lo, hi] of keys (along direction k, in the source leaf's frame,
+// where keys are sorted) that can reach any of the warp's targets: lanes pass
+// their key d_i (target frame) and reach R_i (<= 0 or an inactive lane: no
+// contribution). `sd` = shift . e_k maps source keys into the target frame.
+// Returns false when no lane is active. The pad covers FP32 rounding of the
+// keys and the shift (relative 1e-5 of the magnitudes involved).
+__device__ __forceinline__ bool warp_key_window(bool act, float d, float R, float sd, float &lo,
+                                                float &hi) {
+  float l = act ? d - R : 3e38f, h = act ? d + R : -3e38f;
+  float mag = act ? fabsf(d) + R : 0.f;
+  for (int o = 16; o; o >>= 1) {
+    l = fminf(l, __shfl_xor_sync(0xffffffffu, l, o));
+    h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+    mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+  }
+  if (!(l <= h)) return false;
+  const float pad = 1e-5f * (mag + fabsf(sd)) + 1e-30f;
+  lo = l - sd - pad;
+  hi = h - sd + pad;
+  return true;
+}
+
+// Sorted-rank range [r0, r1) of a source leaf's keys (count entries from
+// `key`) inside [lo, hi]: counted by warp ballots over coalesced loads (keys
+// ascend, so the counts are the bounds).
+__device__ __forceinline__ void warp_key_range(const float *key, int count, float lo, float hi,
+                                               int &r0, int &r1) {
+  const int lane = threadIdx.x & 31;
+  int below = 0, upto = 0;
+  for (int b = 0; b < count; b += 32) {
+    const int k = b + lane;
+    const float v = k < count ? key[k] : 3e38f;
+    below += __popc(__ballot_sync(0xffffffffu, k < count && v < lo));
+    upto += __popc(__ballot_sync(0xffffffffu, k < count && v <= hi));
+  }
+  r0 = below;
+  r1 = upto;
+}
+
 // Target group of the batched kernels: up to 32 consecutive particles (sorted
 // order) of one top cell, one warp lane each.
 struct Group {
@@ -245,6 +326,20 @@ void launch_leaf_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s);
 void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s);
 void launch_h_guess(const GeomArgs &a, double n_ngb, double *h, float *hf, cudaStream_t s);
 
+// ---- axis_sort.cu ----
+struct AxisSortArgs {
+  int n_leaves;
+  const Leaf *leaves;
+  const float4 *pm;     // leaf-relative positions (sorted order)
+  int n;                // particles (stride of one direction's arrays)
+  float *skey;          // out: [kAxes][n] keys in rank order within each leaf
+  int *sidx;            // out: [kAxes][n] leaf-local index of each rank
+};
+void launch_axis_sort(const AxisSortArgs &a, cudaStream_t s);
+void launch_get_pair_order(const Leaf *leaves, const int *leaf_of, const int *sidx,
+                           const int *orig, int n, int axis, int *order_out, int *leaf_out,
+                           cudaStream_t s);
+
 // per-box largest h (dmax[nb]) and global min / max (dminmax[2]), as ordered
 // int64 bit patterns of non-negative doubles (dminmax[0] holds the minimum)
 void launch_h_extremes(const double *h, int n, const BoxDev *boxes, int n_boxes,
@@ -285,6 +380,9 @@ struct DensArgs {
   int *cnt;
   DevCounters *ctr;
   int kahan;
+  const float *skey;     // pair-axis sorts ([kAxes][n]); null: visit whole source leaves
+  const int *sidx;
+  int n;
 };
 void launch_density(const DensArgs &a, cudaStream_t s);
 
@@ -331,6 +429,10 @@ struct ForceArgs {
   int *nforce;
   DevCounters *ctr;
   int kahan;
+  const Node *nodes;      // source-leaf largest h (reach of a pair along a sort axis)
+  const float *skey;      // pair-axis sorts ([kAxes][n]); null: visit whole source leaves
+  const int *sidx;
+  int n;
 };
 void launch_force(const ForceArgs &a, cudaStream_t s);
 

@@ -45,7 +45,7 @@ class sph_params(ctypes.Structure):
                 ("h_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("n_split", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mode", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("pair_sort", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -65,7 +65,10 @@ class sph_stats_t(ctypes.Structure):
                 ("force_launches", ctypes.c_int64),
                 ("t_grid_ms", ctypes.c_double), ("t_lists_ms", ctypes.c_double),
                 ("t_density_ms", ctypes.c_double), ("t_ghost_ms", ctypes.c_double),
-                ("t_force_ms", ctypes.c_double), ("t_integrate_ms", ctypes.c_double)]
+                ("t_force_ms", ctypes.c_double), ("t_integrate_ms", ctypes.c_double),
+                ("t_sort_ms", ctypes.c_double),
+                ("direct_list_warps", ctypes.c_int32), ("direct_stage_warps", ctypes.c_int32),
+                ("fallback_causes", ctypes.c_int32 * 4), ("sort_launches", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):
@@ -106,13 +109,15 @@ def lib(build_if_needed: bool = True):
         L.sph_force.argtypes = [P]
         L.sph_step.argtypes = [P, D, I]
         L.sph_get.argtypes = [P, I, P]
+        L.sph_get_pair_order.argtypes = [P, I, P, P]
         L.sph_stats.argtypes = [P, ctypes.POINTER(sph_stats_t)]
         L.sph_last_error.argtypes = [P]
         L.sph_last_error.restype = ctypes.c_char_p
         L.sph_destroy.argtypes = [P]
         L.sph_destroy.restype = None
         for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
-                  "sph_density", "sph_force", "sph_step", "sph_get", "sph_stats"):
+                  "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
+                  "sph_stats"):
             getattr(L, f).restype = I
         _lib = L
         return L
@@ -199,10 +204,24 @@ def sph_get(ctx, field: int, out) -> None:
     _check(ctx, lib().sph_get(ctx, int(field), ctypes.c_void_p(_ptr(out))), "sph_get")
 
 
+def sph_get_pair_order(ctx, axis: int, order_out, leaf_out) -> None:
+    """order_out, leaf_out: int32 CUDA tensors of N entries (store slot order)."""
+    for t in (order_out, leaf_out):
+        if not t.is_cuda or str(t.dtype) != "torch.int32" or not t.is_contiguous():
+            raise TypeError("expected contiguous CUDA int32 tensors")
+    _check(ctx, lib().sph_get_pair_order(ctx, int(axis), ctypes.c_void_p(_ptr(order_out)),
+                                         ctypes.c_void_p(_ptr(leaf_out))),
+           "sph_get_pair_order")
+
+
 def sph_stats(ctx) -> dict:
     s = sph_stats_t()
     _check(ctx, lib().sph_stats(ctx, ctypes.byref(s)), "sph_stats")
-    return {name: getattr(s, name) for name, _ in sph_stats_t._fields_ if name != "reserved"}
+    out = {}
+    for name, _ in sph_stats_t._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def sph_last_error(ctx) -> str:
@@ -244,15 +263,16 @@ class Context:
     fields back as torch tensors in caller order."""
 
     def __init__(self, n_split: int = 64, precision: int = SPH_PREC_FP32,
-                 mode: int = SPH_MODE_PLAIN, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
-                 h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False, stream=None,
-                 device="cuda"):
+                 mode: int = SPH_MODE_BATCHED, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
+                 h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False,
+                 pair_sort: bool = True, stream=None, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         p = sph_default_params()
         p.n_split, p.precision, p.mode = n_split, precision, mode
         p.profile = int(bool(profile))
+        p.pair_sort = int(bool(pair_sort))
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream
@@ -300,6 +320,13 @@ class Context:
         out = self.torch.empty(shape, dtype=getattr(self.torch, dtype), device=self.device)
         sph_get(self.ctx, f, out)
         return out
+
+    def pair_order(self, axis: int):
+        """(order, leaf) int32 tensors of the pair-axis sort along `axis`."""
+        order = self.torch.empty(self.n, dtype=self.torch.int32, device=self.device)
+        leaf = self.torch.empty(self.n, dtype=self.torch.int32, device=self.device)
+        sph_get_pair_order(self.ctx, axis, order, leaf)
+        return order, leaf
 
     def stats(self) -> dict:
         return sph_stats(self.ctx)

@@ -19,8 +19,8 @@ def libpath():
 def test_header_declares_the_boundary():
     names = sph.header_functions()
     for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
-              "sph_density", "sph_force", "sph_step", "sph_get", "sph_stats",
-              "sph_last_error", "sph_destroy", "sph_default_params"):
+              "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
+              "sph_stats", "sph_last_error", "sph_destroy", "sph_default_params"):
         assert f in names
 
 
@@ -44,9 +44,19 @@ def test_params_struct_matches_header_defaults(libpath):
     p = sph.sph_default_params()
     assert p.gamma == pytest.approx(5.0 / 3.0)
     assert p.n_ngb == 48.0 and p.h_tol == 1e-6 and p.max_iter == 30 and p.n_split == 64
+    assert p.mode == sph.SPH_MODE_BATCHED and p.precision == sph.SPH_PREC_FP32
+    assert p.pair_sort == 1 and p.profile == 0
     assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4
-    assert [f for f, _ in sph.sph_params._fields_][-2:] == ["profile", "reserved"]
-    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 6 * 8
+    assert [f for f, _ in sph.sph_params._fields_][-3:] == ["profile", "pair_sort", "reserved"]
+    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 4 * 4 + 8
+
+
+def test_param_pair_sort_validated(libpath):
+    L = sph.lib()
+    bad = sph.sph_default_params()
+    bad.pair_sort = 2
+    ctx = ctypes.c_void_p()
+    assert L.sph_create(ctypes.byref(ctx), ctypes.byref(bad), None) == sph.SPH_EINVAL
 
 
 def test_invalid_arguments_rejected_without_gpu(libpath):
