@@ -356,25 +356,39 @@ constexpr int kSub = 8;          // targets per warp
 constexpr int kSlice = 4;        // lanes per target
 constexpr int kStageD = 1280;    // density stage entries per group
 constexpr int kStageF = 1024;    // force stage entries per group
+constexpr int kBigStageD = 4096; // second tier: groups whose stage overflowed the first
+constexpr int kBigStageF = 3072;
 constexpr int kCandD = 1280;     // density entries kept per warp
 constexpr int kCandF = 640;      // force entries kept per warp
 constexpr int kLane = 32;        // list entries per lane
 
+template <int NS>
 struct DensSmem {
-  float4 stage[kStageD];                    // position in the group frame, m
+  float4 stage[NS];                         // position in the group frame, m
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][kLane * 32];     // [entry][lane]
   int wcount[kNW];
 };
 
+template <int NS>
 struct ForceSmem {
-  float4 sq[kStageF];                       // position in the group frame, m
-  float2 sf[kStageF];                       // A (8/pi) h^-4, h^2
-  int sj[kStageF];                          // particle index (velocity read on use)
+  float4 sq[NS];                            // position in the group frame, m
+  float2 sf[NS];                            // A (8/pi) h^-4, h^2
+  int sj[NS];                               // particle index (velocity read on use)
   unsigned short cand[kNW][kCandF];
   unsigned short list[kNW][kLane * 32];
   int wcount[kNW];
 };
+
+// Group g of a launch: tier 0 walks every group; tier 1 walks the groups
+// tier 0 queued because their stage outgrew it (count read on the device,
+// so the second launch needs no host round trip).
+__device__ __forceinline__ int tier_group(int tier, int q, const int *queue) {
+  return tier == 0 ? q : queue[q];
+}
+__device__ __forceinline__ int tier_count(int tier, int n_groups, const int *queued) {
+  return tier == 0 ? n_groups : *queued;
+}
 
 struct StageRange {
   int base, count, total;  // this warp's entries [base, base + count); all warps' total
@@ -584,10 +598,11 @@ struct DensAcc {
   }
 };
 
-template <bool KAHAN>
-__global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a) {
+template <bool KAHAN, int NS>
+__global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
+    k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  DensSmem &S = *reinterpret_cast<DensSmem *>(smem_raw);
+  DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
@@ -596,7 +611,9 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
   int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
   int why[3] = {0, 0, 0};  // fallback causes: stage/task overflow, h beyond the stage, passes
 
-  for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
+  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
+  for (int q = blockIdx.x; q < ng; q += gridDim.x) {
+    const int g = tier_group(tier, q, a.queue);
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
@@ -605,9 +622,14 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
     const StageRange sr = stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane,
-                                             Rg, S.stage, nullptr, nullptr, S.wcount, kStageD);
+                                             Rg, S.stage, nullptr, nullptr, S.wcount, NS);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > kStageD || nt > a.tcap) {  // block-uniform: the group goes to the per-pass form
+    if (sr.total > NS || nt > a.tcap) {  // block-uniform
+      if (tier == 0 && nt <= a.tcap && sr.total <= kBigStageD) {
+        if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[0], 1)] = g;
+        continue;  // the second tier stages it whole
+      }
+      // the group goes to the per-pass form
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
         ++fallback, ++why[0];
       continue;
@@ -770,24 +792,33 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_density_batched(BatchDensArgs a
   }
 }
 
-void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
-  if (a.n_groups <= 0) return;
+template <bool KAHAN, int NS>
+void launch_density_tier(const BatchDensArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
-  const int bytes = (int)sizeof(DensSmem);
+  const int bytes = (int)sizeof(DensSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_density_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
-    cudaFuncSetAttribute(k_density_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
+    cudaFuncSetAttribute(k_density_batched<KAHAN, NS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
-  int blocks = a.n_groups;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  if (a.kahan)
-    k_density_batched<true><<<blocks, kNW * 32, bytes, s>>>(a);
-  else
-    k_density_batched<false><<<blocks, kNW * 32, bytes, s>>>(a);
+  k_density_batched<KAHAN, NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
+}
+
+// Tier 0 over every group, then tier 1 (4x the stage, 2 blocks per SM) over
+// the groups tier 0 queued; `a.ctr->queued` and `a.queue` must be zeroed /
+// sized for n_groups by the caller.
+void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
+  const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
+  if (a.kahan) {
+    launch_density_tier<true, kStageD>(a, 0, blocks, s);
+    launch_density_tier<true, kBigStageD>(a, 1, big, s);
+  } else {
+    launch_density_tier<false, kStageD>(a, 0, blocks, s);
+    launch_density_tier<false, kBigStageD>(a, 1, big, s);
+  }
 }
 
 // One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
@@ -796,7 +827,8 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
 struct ForceAcc {
   float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
   int c = 0;
-  __device__ __forceinline__ void add(const ForceSmem &S, int k, const float4 *vu, float px,
+  template <class SM>
+  __device__ __forceinline__ void add(const SM &S, int k, const float4 *vu, float px,
                                       float py, float pz, float4 fi, float4 vi, float hi2) {
     const float4 q = S.sq[k];
     const float2 f = S.sf[k];
@@ -818,9 +850,11 @@ struct ForceAcc {
   }
 };
 
-__global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a) {
+template <int NS>
+__global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
+    k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ForceSmem &S = *reinterpret_cast<ForceSmem *>(smem_raw);
+  ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
@@ -829,14 +863,20 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
   int fallback = 0, stage_max = 0, n_direct[2] = {0, 0};
   int why0 = 0;  // fallbacks for stage or task overflow
 
-  for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
+  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
+  for (int q = blockIdx.x; q < ng; q += gridDim.x) {
+    const int g = tier_group(tier, q, a.queue);
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
     const StageRange sr = stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane,
-                                            G.hmax, S.sq, S.sf, S.sj, S.wcount, kStageF);
+                                            G.hmax, S.sq, S.sf, S.sj, S.wcount, NS);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > kStageF || nt > a.tcap) {  // block-uniform
+    if (sr.total > NS || nt > a.tcap) {  // block-uniform
+      if (tier == 0 && nt <= a.tcap && sr.total <= kBigStageF) {
+        if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[1], 1)] = g;
+        continue;  // the second tier stages it whole
+      }
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
         ++fallback, ++why0;
       continue;
@@ -932,18 +972,24 @@ __global__ void __launch_bounds__(kNW * 32, 5) k_force_batched(BatchForceArgs a)
   if (lane == 0 && why0) atomicAdd(&a.ctr->why[3], why0);
 }
 
-void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
-  if (a.n_groups <= 0) return;
+template <int NS>
+void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
-  const int bytes = (int)sizeof(ForceSmem);
+  const int bytes = (int)sizeof(ForceSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_force_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_force_batched<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
-  int blocks = a.n_groups;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  k_force_batched<<<blocks, kNW * 32, bytes, s>>>(a);
+  k_force_batched<NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
+}
+
+void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
+  if (a.n_groups <= 0) return;
+  const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
+  const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
+  launch_force_tier<kStageF>(a, 0, blocks, s);
+  launch_force_tier<kBigStageF>(a, 1, big, s);
 }
 
 }  // namespace sph

@@ -158,29 +158,49 @@ __device__ __forceinline__ void cell_coords(const BoxDev &B, int local, int c[3]
 
 // ------------------------------------------------------------------ A1
 
+// Lanes of the warp whose `key` equals this lane's, and this lane's rank
+// among them (inactive lanes pass a key no active lane uses).
+__device__ __forceinline__ unsigned warp_peers(int key, int &rank) {
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+  return peers;
+}
+
 // Integer top-cell key and 30-bit Morton code (10 bits per axis inside the
-// top cell) of every particle, plus the cell histogram.
+// top cell) of every particle, plus the cell histogram. The cell index is
+// floor(x / w) exactly (a product with 1/w, corrected by one step either way
+// in FP64), so rel = x - c w lies in [0, w). Histogram increments are
+// aggregated over the lanes of a warp that share a cell.
 __global__ void k_cell_keys(GridArgs g) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= g.n) return;
-  const BoxDev &B = g.boxes[box_of_particle(g.boxes, g.n_boxes, k)];
-  const double x[3] = {g.x0[k], g.x1[k], g.x2[k]};
-  int ic[3];
-  unsigned q[3];
+  const bool valid = k < g.n;
+  int cell = -1;
+  if (valid) {
+    const BoxDev &B = g.boxes[box_of_particle(g.boxes, g.n_boxes, k)];
+    const double x[3] = {g.x0[k], g.x1[k], g.x2[k]};
+    int ic[3];
+    unsigned q[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int c = (int)floor(x[d] / B.w[d]);
-    c = c < 0 ? 0 : (c >= B.n[d] ? B.n[d] - 1 : c);
-    ic[d] = c;
-    const double rel = x[d] - (double)c * B.w[d];
-    int qi = (int)floor(rel / B.w[d] * (double)(1 << kMaxDepth));
-    qi = qi < 0 ? 0 : (qi > (1 << kMaxDepth) - 1 ? (1 << kMaxDepth) - 1 : qi);
-    q[d] = (unsigned)qi;
+    for (int d = 0; d < 3; ++d) {
+      int c = (int)floor(x[d] * B.iw[d]);
+      if ((double)c * B.w[d] > x[d])
+        --c;
+      else if ((double)(c + 1) * B.w[d] <= x[d])
+        ++c;
+      c = c < 0 ? 0 : (c >= B.n[d] ? B.n[d] - 1 : c);
+      ic[d] = c;
+      const double rel = x[d] - (double)c * B.w[d];
+      int qi = (int)floor(rel * (B.iw[d] * (double)(1 << kMaxDepth)));
+      qi = qi < 0 ? 0 : (qi > (1 << kMaxDepth) - 1 ? (1 << kMaxDepth) - 1 : qi);
+      q[d] = (unsigned)qi;
+    }
+    cell = B.cell_base + (ic[0] * B.n[1] + ic[1]) * B.n[2] + ic[2];
+    g.cell_of[k] = cell;
+    g.morton[k] = (part1by2(q[0]) << 2) | (part1by2(q[1]) << 1) | part1by2(q[2]);
   }
-  const int cell = B.cell_base + (ic[0] * B.n[1] + ic[1]) * B.n[2] + ic[2];
-  g.cell_of[k] = cell;
-  g.morton[k] = (part1by2(q[0]) << 2) | (part1by2(q[1]) << 1) | part1by2(q[2]);
-  atomicAdd(&g.cell_count[cell], 1);
+  int rank;
+  const unsigned peers = warp_peers(cell, rank);
+  if (valid && rank == 0) atomicAdd(&g.cell_count[cell], __popc(peers));
 }
 
 void launch_cell_keys(const GridArgs &g, cudaStream_t s) {
@@ -192,9 +212,15 @@ void launch_cell_keys(const GridArgs &g, cudaStream_t s) {
 // cursor does not make the final order depend on timing.
 __global__ void k_cell_scatter(GridArgs g) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= g.n) return;
-  const int c = g.cell_of[k];
-  const int pos = g.cell_start[c] + atomicAdd(&g.cursor[c], 1);
+  const bool valid = k < g.n;
+  const int c = valid ? g.cell_of[k] : -1;
+  int rank;
+  const unsigned peers = warp_peers(c, rank);
+  int base = 0;
+  if (valid && rank == 0) base = atomicAdd(&g.cursor[c], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, __ffs(peers) - 1);
+  if (!valid) return;
+  const int pos = g.cell_start[c] + base + rank;
   g.order[pos] = k;
   g.morton_tmp[pos] = g.morton[k];
 }
@@ -354,19 +380,25 @@ void launch_fill_leaves(Node *nodes, int n_nodes, const int *leaf_idx_excl, Leaf
                                                       boxes, n_boxes); note_launch();
 }
 
-// Order each leaf's particles by original index (insertion sort; leaves are
-// small), so the slot order never depends on atomic timing.
-__global__ void k_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig) {
+// Order each leaf's particles by (Morton code inside the top cell, original
+// index) (insertion sort; leaves are small): the slot order never depends on
+// atomic timing, and consecutive slots stay spatially close, so the batched
+// kernels' groups of 32 consecutive particles are compact.
+__global__ void k_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig,
+                              const unsigned *morton) {
   const int li = blockIdx.x * blockDim.x + threadIdx.x;
   if (li >= n_leaves) return;
   const Leaf L = leaves[li];
   if (L.count > 512) return;
   int *o = order + L.start;
+  auto key_of = [&](int v) {
+    return ((unsigned long long)morton[v] << 32) | (unsigned)orig[v];
+  };
   for (int a = 1; a < L.count; ++a) {
     const int v = o[a];
-    const int key = orig[v];
+    const unsigned long long key = key_of(v);
     int b = a - 1;
-    while (b >= 0 && orig[o[b]] > key) {
+    while (b >= 0 && key_of(o[b]) > key) {
       o[b + 1] = o[b];
       --b;
     }
@@ -375,8 +407,9 @@ __global__ void k_sort_leaves(const Leaf *leaves, int n_leaves, int *order, cons
 }
 
 void launch_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig,
-                        cudaStream_t s) {
-  k_sort_leaves<<<(n_leaves + 127) / 128, 128, 0, s>>>(leaves, n_leaves, order, orig); note_launch();
+                        const unsigned *morton, cudaStream_t s) {
+  k_sort_leaves<<<(n_leaves + 127) / 128, 128, 0, s>>>(leaves, n_leaves, order, orig, morton);
+  note_launch();
 }
 
 // --------------------------------------------------- leaf geometry / hmax

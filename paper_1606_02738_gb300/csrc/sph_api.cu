@@ -68,7 +68,7 @@ struct sph_ctx {
 
   // growable, library-owned
   // batched form: target groups and their task lists
-  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks;
+  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue;
   int n_groups = 0;
   bool groups_valid = false;
   int64_t n_gd_tasks = 0, n_gf_tasks = 0;
@@ -343,6 +343,7 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
       for (int d = 0; d < 3; ++d) {
         B.n[d] = 3;
         B.w[d] = B.L[d] / 3.0;
+        B.iw[d] = 1.0 / B.w[d];
       }
       B.eps = (float)(1e-5 * std::max(B.w[0], std::max(B.w[1], B.w[2])));
       B.cell_base = base;
@@ -372,6 +373,7 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
     double wmax = 0.0;
     for (int d = 0; d < 3; ++d) {
       B.w[d] = B.L[d] / B.n[d];
+      B.iw[d] = 1.0 / B.w[d];
       wmax = std::max(wmax, B.w[d]);
     }
     B.eps = (float)(1e-5 * wmax);
@@ -492,7 +494,7 @@ int build_grid_inner(sph_ctx *c, bool from_caller, const float *cv, const float 
   TRY(ensure(c, c->active, sizeof(int) * (size_t)(nl + 1)));
   launch_fill_leaves(as<Node>(c->nodes), n_nodes, c->excl, as<Leaf>(c->leaves), c->boxes_d, c->nb,
                      c->stream);
-  launch_sort_leaves(as<Leaf>(c->leaves), nl, c->order, g.orig, c->stream);
+  launch_sort_leaves(as<Leaf>(c->leaves), nl, c->order, g.orig, g.morton, c->stream);
 
   // gather the store into leaf order
   if (from_caller) {
@@ -627,6 +629,7 @@ int build_groups(sph_ctx *c) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->n_groups = ng;
   TRY(ensure(c, c->groups, sizeof(Group) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1)));
   ga = group_args(c);
   launch_group_fill(ga, c->stream);
   launch_group_geometry(ga, c->stream);
@@ -701,6 +704,7 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   da.P = c->P;
   da.fi = c->fi;
   da.ctr = c->ctr;
+  da.queue = as<int>(c->gqueue);  // ctr->queued was zeroed with the counters
   tic(c, kDens);
   launch_density_batched(da, c->stream);
   toc(c, kDens);
@@ -829,6 +833,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
@@ -845,6 +850,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   fa.nforce = c->nforce;
   fa.fdone = c->fdone;
   fa.ctr = c->ctr;
+  fa.queue = as<int>(c->gqueue);
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -1160,7 +1166,8 @@ void sph_destroy(sph_ctx *c) {
   DevBuf *bufs[] = {&c->cell_count, &c->cell_start, &c->cursor,   &c->nodes,      &c->frontier,
                     &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
-                    &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks};
+                    &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
+                    &c->gqueue};
   for (DevBuf *b : bufs) release(*b);
   for (void *p : c->owned) cudaFree(p);
   if (c->ctr) cudaFree(c->ctr);

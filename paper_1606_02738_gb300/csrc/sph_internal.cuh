@@ -42,6 +42,7 @@ struct BoxDev {
   int first, count;  // particle range (the same in caller and sorted order)
   float eps;       // pruning margin in top-cell-relative units
   float pad;
+  double iw[3];    // 1 / w
 };
 
 struct Node {
@@ -86,6 +87,7 @@ struct DevCounters {
   int stage_max[2];                   // largest group stage (density, force) of the batched form
   int direct[2];                      // batched warp-groups that read their candidates
                                       // directly (a list overflowed) / the whole stage
+  int queued[2];                      // groups queued for the second (larger-stage) tier
   int why[4];                         // batched fallbacks: density stage or task overflow,
                                       // density h beyond the stage, density passes, force
                                       // stage or task overflow
@@ -309,7 +311,7 @@ void launch_mark_leaves(const Node *nodes, int n_nodes, int *flag, cudaStream_t 
 void launch_fill_leaves(Node *nodes, int n_nodes, const int *leaf_idx_excl, Leaf *leaves,
                         const BoxDev *boxes, int n_boxes, cudaStream_t s);
 void launch_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int *orig,
-                        cudaStream_t s);
+                        const unsigned *morton, cudaStream_t s);
 
 struct GeomArgs {
   int n_leaves;
@@ -495,6 +497,7 @@ struct BatchDensArgs {
   float *rho, *omega, *P;
   float4 *fi;
   DevCounters *ctr;
+  int *queue;            // [n_groups] groups handed to the second tier
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 
@@ -513,6 +516,7 @@ struct BatchForceArgs {
   int *nforce;
   unsigned char *fdone;  // per particle: force written by the batched kernel
   DevCounters *ctr;
+  int *queue;            // [n_groups] groups handed to the second tier
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 
