@@ -136,11 +136,11 @@ typedef struct {
   int32_t direct_list_warps;
   int32_t direct_stage_warps;
   /* Particles of the last sph_density + sph_force that the batched kernels
-   * left to the per-pass form, by cause: [0] density group stage or task
-   * slots overflowed, [1] a density h grew beyond the staged radius, [2] an
-   * h not converged in max_iter passes, [3] force group stage or task slots
-   * overflowed. */
-  int32_t fallback_causes[4];
+   * left to the per-pass form, by cause: [0] density group stage overflowed
+   * (both tiers), [1] a density h grew beyond the staged radius, [2] an h not
+   * converged in max_iter passes, [3] force group stage overflowed, [4] / [5]
+   * density / force group task slots overflowed. */
+  int32_t fallback_causes[6];
   int64_t sort_launches;      /* pair-axis sort launches (cumulative since sph_create) */
 } sph_stats_t;
 

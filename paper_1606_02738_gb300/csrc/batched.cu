@@ -390,124 +390,146 @@ __device__ __forceinline__ int tier_count(int tier, int n_groups, const int *que
   return tier == 0 ? n_groups : *queued;
 }
 
+// The stage is laid out in kNW segments of cap / kNW entries, warp w's staged
+// particles in segment w in the order that warp found them (deterministic).
+// A flat index t in [0, total) maps to segment entries through the prefix
+// counts pre[].
 struct StageRange {
-  int base, count, total;  // this warp's entries [base, base + count); all warps' total
+  int total;      // staged entries, all warps
+  int over;       // some warp's share outgrew its segment (the stage is incomplete)
+  int maxw;       // largest warp share
+  int segcap;     // entries per segment
+  int pre1, pre2, pre3;  // prefix counts of segments 0, 0..1, 0..2
+  __device__ __forceinline__ int index(int t) const {
+    const int off = t >= pre3 ? 3 * segcap - pre3
+                              : (t >= pre2 ? 2 * segcap - pre2 : (t >= pre1 ? segcap - pre1 : 0));
+    return t + off;
+  }
 };
 
+constexpr int kMap = 1024;  // per-warp particle -> task map (bytes, aliases the warp's cand)
+static_assert(kCandD * 2 >= kMap && kCandF * 2 >= kMap, "task map must fit a warp's cand");
+static_assert(kStageD % kNW == 0 && kStageF % kNW == 0 && kBigStageD % kNW == 0 &&
+                  kBigStageF % kNW == 0, "stage segments");
+
 // Stage the particles of this warp's share of the group's source leaves that
-// lie within R of the group box (R = Rg, or max(Rg, h_j) for the force). The
-// warp takes 32 of its tasks at a time, one per lane; a warp scan of their
-// particle counts gives each task's offset, and the lanes then walk the
-// concatenated particles 32 at a time (a particle finds its task by a 5-step
-// shuffle search), so lanes stay busy however small the leaves are. A count
-// pass sizes each warp's share, the shares are laid out in warp order, and a
-// write pass fills them: the stage order never depends on timing. Called by
-// every thread of the block; total > cap means overflow.
+// lie within R of the group box (R = Rg, or max(Rg, h_j) for the force), in
+// one pass. The warp takes 32 of its tasks at a time, one per lane; a warp
+// scan of their particle counts lays the 32 leaves end to end, each lane
+// marks its leaf's stretch in a shared-memory map, and the lanes then walk
+// the concatenated particles 32 at a time (kU loads in flight), reading each
+// particle's task from the map and the task's base and shift by shuffles.
+// Passing particles are appended to the warp's segment by ballot. Called by
+// every thread of the block.
 template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
-                                  float4 *sq, float2 *sf, int *sj, int *wcount, int cap) {
+                                  float4 *sq, float2 *sf, int *sj, int *wcount,
+                                  unsigned char *tmap, int cap) {
   const unsigned ltmask = (1u << lane) - 1u;
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
   const float4 *pm = FORCE ? fa->pm : da->pm;
   const int ntask = e1 - e0;
-  StageRange r;
-  r.base = 0;
-  r.count = 0;
-  r.total = 0;
-  for (int write = 0; write < 2; ++write) {
-    int nst = 0;
-    for (int tb = warp; tb < ntask; tb += 32 * kNW) {
-      const int mt = tb + lane * kNW;  // this lane's task
-      int start = 0, cnt = 0;
-      float sx = 0.f, sy = 0.f, sz = 0.f;
-      if (mt < ntask) {
-        const Task tk = tasks[e0 + mt];
-        const Leaf &LS = leaves[tk.src];
-        start = LS.start;
-        cnt = LS.count;
-        sx = tk.sx;
-        sy = tk.sy;
-        sz = tk.sz;
-      }
-      int incl = cnt;  // inclusive scan over the lanes
+  const int segcap = cap / kNW;
+  const int base = warp * segcap;
+  __syncthreads();  // every warp is done with the previous group's stage
+  int nst = 0;
+  for (int tb = warp; tb < ntask; tb += 32 * kNW) {
+    const int mt = tb + lane * kNW;  // this lane's task
+    int start = 0, cnt = 0;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (mt < ntask) {
+      const Task tk = tasks[e0 + mt];
+      const Leaf &LS = leaves[tk.src];
+      start = LS.start;
+      cnt = LS.count;
+      sx = tk.sx;
+      sy = tk.sy;
+      sz = tk.sz;
+    }
+    int incl = cnt;  // inclusive scan over the lanes
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      constexpr int kU = 4;  // chunks whose loads are in flight together
-      for (int f0 = 0; f0 < total; f0 += 32 * kU) {
-        float4 q[kU], fj[kU];
-        int jj[kU];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int jbase = start - (incl - cnt);  // particle of flat index f: jbase_t + f
+    const bool mapped = total <= kMap;       // warp-uniform
+    if (mapped) {
+      for (int f = incl - cnt; f < incl; ++f) tmap[f] = (unsigned char)lane;
+      __syncwarp();
+    }
+    constexpr int kU = 4;  // chunks whose loads are in flight together
+    for (int f0 = 0; f0 < total; f0 += 32 * kU) {
+      float4 q[kU], fj[kU];
+      int jj[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int f = f0 + 32 * u + lane;
-          int t = 0;  // first task whose inclusive count exceeds f
+      for (int u = 0; u < kU; ++u) {
+        const int f = f0 + 32 * u + lane;
+        int t = 0;
+        if (mapped) {
+          t = f < total ? tmap[f] : 0;
+        } else {  // first task whose inclusive count exceeds f
 #pragma unroll
           for (int s = 16; s; s >>= 1) {
             const int v = __shfl_sync(0xffffffffu, incl, t + s - 1);
             if (v <= f) t += s;
           }
-          const int t_incl = __shfl_sync(0xffffffffu, incl, t);
-          const int t_cnt = __shfl_sync(0xffffffffu, cnt, t);
-          const int t_start = __shfl_sync(0xffffffffu, start, t);
-          const float tx = __shfl_sync(0xffffffffu, sx, t);
-          const float ty = __shfl_sync(0xffffffffu, sy, t);
-          const float tz = __shfl_sync(0xffffffffu, sz, t);
-          jj[u] = t_start + f - (t_incl - t_cnt);
-          q[u] = make_float4(tx, ty, tz, 0.f);
-          fj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (f < total) {
-            const float4 p4 = pm[jj[u]];
-            q[u].x += p4.x;
-            q[u].y += p4.y;
-            q[u].z += p4.z;
-            q[u].w = p4.w;
-            if (FORCE) fj[u] = fa->fi[jj[u]];
-          }
         }
+        const int tb0 = __shfl_sync(0xffffffffu, jbase, t);
+        const float tx = __shfl_sync(0xffffffffu, sx, t);
+        const float ty = __shfl_sync(0xffffffffu, sy, t);
+        const float tz = __shfl_sync(0xffffffffu, sz, t);
+        jj[u] = tb0 + f;
+        q[u] = make_float4(tx, ty, tz, 0.f);
+        fj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (f < total) {
+          const float4 p4 = pm[jj[u]];
+          q[u].x += p4.x;
+          q[u].y += p4.y;
+          q[u].z += p4.z;
+          q[u].w = p4.w;
+          if (FORCE) fj[u] = fa->fi[jj[u]];
+        }
+      }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int f = f0 + 32 * u + lane;
-          bool in = false;
-          if (f < total) {
-            const float R = FORCE ? fmaxf(Rg, fj[u].x) : Rg;
-            const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q[u].x, q[u].x - G.fhi[0]));
-            const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q[u].y, q[u].y - G.fhi[1]));
-            const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q[u].z, q[u].z - G.fhi[2]));
-            in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, in);
-          if (write) {
-            const int pos = r.base + nst + __popc(m & ltmask);
-            if (in && pos < cap) {
-              sq[pos] = q[u];
-              if (FORCE) {
-                sf[pos] = make_float2(fj[u].z, fj[u].w);
-                sj[pos] = jj[u];
-              }
-            }
-          }
-          nst += __popc(m);
+      for (int u = 0; u < kU; ++u) {
+        const int f = f0 + 32 * u + lane;
+        bool in = false;
+        if (f < total) {
+          const float R = FORCE ? fmaxf(Rg, fj[u].x) : Rg;
+          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q[u].x, q[u].x - G.fhi[0]));
+          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q[u].y, q[u].y - G.fhi[1]));
+          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q[u].z, q[u].z - G.fhi[2]));
+          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        const int pos = nst + __popc(m & ltmask);
+        if (in && pos < segcap) {
+          sq[base + pos] = q[u];
+          if (FORCE) {
+            sf[base + pos] = make_float2(fj[u].z, fj[u].w);
+            sj[base + pos] = jj[u];
+          }
+        }
+        nst += __popc(m);
       }
     }
-    if (!write) {
-      if (lane == 0) wcount[warp] = nst;
-      __syncthreads();
-      for (int w = 0; w < kNW; ++w) {
-        if (w < warp) r.base += wcount[w];
-        r.total += wcount[w];
-      }
-      r.count = nst;
-      __syncthreads();
-      if (r.total > cap) break;  // block-uniform
-    }
+    if (mapped) __syncwarp();  // the map is rewritten by the next 32 tasks
   }
+  if (lane == 0) wcount[warp] = nst;
   __syncthreads();
+  StageRange r;
+  r.segcap = segcap;
+  const int c0 = wcount[0], c1 = wcount[1], c2 = wcount[2], c3 = wcount[3];
+  r.pre1 = c0;
+  r.pre2 = c0 + c1;
+  r.pre3 = c0 + c1 + c2;
+  r.total = r.pre3 + c3;
+  r.maxw = max(max(c0, c1), max(c2, c3));
+  r.over = r.maxw > segcap;
   return r;
 }
 
@@ -533,15 +555,18 @@ __device__ __forceinline__ void sub_box(bool has, float px, float py, float pz, 
 // force max(Rsub, h_j)) of the sub-cluster box, compacted in stage order into
 // `cand`. Returns the count (> cap means overflow).
 template <bool FORCE>
-__device__ __forceinline__ int filter_stage(const float4 *sq, const float2 *sf, int nst,
-                                            const float lo[3], const float hi[3], float Rsub,
-                                            unsigned short *cand, int cap, int lane) {
+__device__ __forceinline__ int filter_stage(const float4 *sq, const float2 *sf,
+                                            const StageRange &sr, const float lo[3],
+                                            const float hi[3], float Rsub, unsigned short *cand,
+                                            int cap, int lane) {
   const unsigned ltmask = (1u << lane) - 1u;
   int n = 0;
-  for (int kb = 0; kb < nst; kb += 32) {
-    const int k = kb + lane;
+  for (int tb = 0; tb < sr.total; tb += 32) {
+    const int t = tb + lane;
     bool in = false;
-    if (k < nst) {
+    int k = 0;
+    if (t < sr.total) {
+      k = sr.index(t);
       const float4 q = sq[k];
       const float R = FORCE ? fmaxf(Rsub, sqrtf(sf[k].y)) : Rsub;
       const float gx = fmaxf(0.f, fmaxf(lo[0] - q.x, q.x - hi[0]));
@@ -609,7 +634,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
   int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
-  int why[3] = {0, 0, 0};  // fallback causes: stage/task overflow, h beyond the stage, passes
+  int why[4] = {0, 0, 0, 0};  // fallbacks: stage overflow, h beyond the stage, passes, tasks
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -621,21 +646,20 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
-    const StageRange sr = stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane,
-                                             Rg, S.stage, nullptr, nullptr, S.wcount, NS);
+    const StageRange sr =
+        stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane, Rg, S.stage,
+                           nullptr, nullptr, S.wcount, (unsigned char *)cand, NS);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > NS || nt > a.tcap) {  // block-uniform
-      if (tier == 0 && nt <= a.tcap && sr.total <= kBigStageD) {
+    if (sr.over || nt > a.tcap) {  // block-uniform
+      if (tier == 0 && nt <= a.tcap && sr.maxw <= kBigStageD / kNW) {
         if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[0], 1)] = g;
         continue;  // the second tier stages it whole
       }
       // the group goes to the per-pass form
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback, ++why[0];
+        ++fallback, ++why[nt > a.tcap ? 3 : 0];
       continue;
     }
-    const int nst = sr.total;
-
     // this warp's targets: lane = target * kSlice + slice
     const int tloc = warp * kSub + (lane >> 2);
     const bool has = tloc < G.count;
@@ -672,7 +696,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
         float hm = has && !fin ? (float)it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
         rsub = fminf(hm * a.skin_stage, Rg);
-        ncand = filter_stage<false>(S.stage, nullptr, nst, blo, bhi, rsub, cand, kCandD, lane);
+        ncand = filter_stage<false>(S.stage, nullptr, sr, blo, bhi, rsub, cand, kCandD, lane);
         need_filter = false;
         need_list = !fin;
         if (ncand > kCandD) mode = 2;  // ncand is warp-uniform
@@ -711,9 +735,9 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
           if (t < cnt && !fin) acc.add(S.stage[list[t * 32 + lane]], px, py, pz, h2, hinv);
         if (!fin) ntest += cnt;
       } else {
-        const int nsrc = mode == 1 ? ncand : nst;
+        const int nsrc = mode == 1 ? ncand : sr.total;
         for (int t = slice; t < nsrc; t += kSlice)
-          acc.add(S.stage[mode == 1 ? (int)cand[t] : t], px, py, pz, h2, hinv);
+          acc.add(S.stage[mode == 1 ? (int)cand[t] : sr.index(t)], px, py, pz, h2, hinv);
         if (!fin) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
       }
       const float4 tot = make_float4(slice_sum(acc.sw), slice_sum(acc.sdw), slice_sum(acc.smw),
@@ -786,9 +810,9 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
     if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     const int w = (int)warp_sum((unsigned long long)why[k]);
-    if (lane == 0 && w) atomicAdd(&a.ctr->why[k], w);
+    if (lane == 0 && w) atomicAdd(&a.ctr->why[k == 3 ? 4 : k], w);
   }
 }
 
@@ -861,7 +885,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
   int fallback = 0, stage_max = 0, n_direct[2] = {0, 0};
-  int why0 = 0;  // fallbacks for stage or task overflow
+  int why0 = 0, why1 = 0;  // fallbacks for stage overflow, for task overflow
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -869,16 +893,17 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
-    const StageRange sr = stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane,
-                                            G.hmax, S.sq, S.sf, S.sj, S.wcount, NS);
+    const StageRange sr =
+        stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane, G.hmax, S.sq,
+                          S.sf, S.sj, S.wcount, (unsigned char *)cand, NS);
     stage_max = max(stage_max, sr.total);
-    if (sr.total > NS || nt > a.tcap) {  // block-uniform
-      if (tier == 0 && nt <= a.tcap && sr.total <= kBigStageF) {
+    if (sr.over || nt > a.tcap) {  // block-uniform
+      if (tier == 0 && nt <= a.tcap && sr.maxw <= kBigStageF / kNW) {
         if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[1], 1)] = g;
         continue;  // the second tier stages it whole
       }
       if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback, ++why0;
+        ++fallback, ++(nt > a.tcap ? why1 : why0);
       continue;
     }
     const int tloc = warp * kSub + (lane >> 2);
@@ -900,7 +925,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     sub_box(has, px, py, pz, blo, bhi);
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-    const int ncand = filter_stage<true>(S.sq, S.sf, sr.total, blo, bhi, hm, cand, kCandF, lane);
+    const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, kCandF, lane);
     // 0: per-lane lists; 1: a list outgrew kLane, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandF, it reads the
     // whole stage (ncand is warp-uniform)
@@ -934,7 +959,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
       const int nsrc = mode == 1 ? ncand : sr.total;
       if (has)
         for (int t = slice; t < nsrc; t += kSlice)
-          acc.add(S, mode == 1 ? (int)cand[t] : t, a.vu, px, py, pz, fi, vi, hi2);
+          acc.add(S, mode == 1 ? (int)cand[t] : sr.index(t), a.vu, px, py, pz, fi, vi, hi2);
       if (has) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
     }
     if (lane == 0 && mode) ++n_direct[mode - 1];
@@ -969,7 +994,9 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
   why0 = (int)warp_sum((unsigned long long)why0);
+  why1 = (int)warp_sum((unsigned long long)why1);
   if (lane == 0 && why0) atomicAdd(&a.ctr->why[3], why0);
+  if (lane == 0 && why1) atomicAdd(&a.ctr->why[5], why1);
 }
 
 template <int NS>

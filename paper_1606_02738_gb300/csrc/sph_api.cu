@@ -1147,7 +1147,7 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->t_sort_ms = c->t_ms[kSort];
   out->direct_list_warps = c->ctr_h->direct[0];
   out->direct_stage_warps = c->ctr_h->direct[1];
-  for (int k = 0; k < 4; ++k) out->fallback_causes[k] = c->ctr_h->why[k];
+  for (int k = 0; k < 6; ++k) out->fallback_causes[k] = c->ctr_h->why[k];
   out->sort_launches = c->sort_launches;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;

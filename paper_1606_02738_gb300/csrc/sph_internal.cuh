@@ -88,9 +88,9 @@ struct DevCounters {
   int direct[2];                      // batched warp-groups that read their candidates
                                       // directly (a list overflowed) / the whole stage
   int queued[2];                      // groups queued for the second (larger-stage) tier
-  int why[4];                         // batched fallbacks: density stage or task overflow,
-                                      // density h beyond the stage, density passes, force
-                                      // stage or task overflow
+  int why[6];                         // batched fallbacks: density stage overflow, density
+                                      // h beyond the stage, density passes, force stage
+                                      // overflow, density / force task-slot overflow
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
