@@ -53,22 +53,35 @@ def parse():
                     help="skip timing the other interaction form for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload's particle count (same recipe) for profiling")
     ap.add_argument("--workload", default="sod", choices=["sod", "uniform", "clustered",
                                                           "batched", "lognormal"])
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, scale=1.0):
+    """(particles, dt, name); dt None: chosen after the first density by cfl_dt."""
     from paper_1606_02738_gb300 import inputs
-    if name == "sod":
-        return inputs.config(2), SOD_DT, "sod3d_972k"
-    if name == "uniform":
-        return inputs.config(1), 1e-3, "uniform_32k"
-    if name == "clustered":
-        return inputs.config(3), 2e-4, "plummer_clustered_4M"
-    if name == "batched":
-        return inputs.config(4), 2e-4, "batched_256_boxes"
-    return inputs.config(5), 2e-4, "lognormal_64M"
+    k = {"uniform": 1, "sod": 2, "clustered": 3, "batched": 4, "lognormal": 5}[name]
+    p = inputs.config(k, scale)
+    tag = {1: "uniform_32k", 2: "sod3d_972k", 3: "plummer_clustered_4M", 4: "batched_256_boxes",
+           5: "lognormal_64M"}[k]
+    if scale != 1.0:
+        tag = f"{tag}_scaled_{p.n}"
+    return p, (SOD_DT if k == 2 else None), tag
+
+
+def cfl_dt(ctx, gamma=5.0 / 3.0):
+    """0.1 min_i h_i / (c_i + |v_i|), c = sqrt(gamma (gamma - 1) u), from the
+    state after the first density (a global step small enough for every
+    particle; the paper's test problems use the same global-step form)."""
+    import torch
+    h = ctx.get("h")
+    u = ctx.get("u").double()
+    v = ctx.get("v").double()
+    c = torch.sqrt(gamma * (gamma - 1.0) * u.clamp_min(0.0))
+    return float(0.1 * (h / (c + v.norm(dim=1))).min())
 
 
 # ----------------------------------------------------------- distributed
@@ -236,7 +249,7 @@ def run_reference(args, d: Dist):
     import numpy as np
     import oracle
     oracle.build()
-    p, dt, wname = workload(args.workload)
+    p, dt, wname = workload(args.workload, args.scale)
     s = oracle.State.from_particles(p)
     oracle.compute_density(s)          # untimed set-up: every h, rho, Omega
     total = args.steps + args.warmup
@@ -280,13 +293,15 @@ def run_ours(args, d: Dist):
         raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
     torch.cuda.set_device(d.local)
     dev = torch.device("cuda", d.local)
-    p, dt, wname = workload(args.workload)
+    p, dt, wname = workload(args.workload, args.scale)
     mode = sph.SPH_MODE_BATCHED if args.mode == "batched" else sph.SPH_MODE_PLAIN
     stream = torch.cuda.current_stream(dev)
     ctx = sph.Context(mode=mode, profile=True, pair_sort=not args.no_pair_sort, device=dev)
     ctx.load(p)
     ctx.density()
     ctx.force()
+    if dt is None:
+        dt = cfl_dt(ctx, p.gamma)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
 
     for _ in range(args.warmup):
@@ -436,6 +451,8 @@ def run_ours(args, d: Dist):
                        "density_passes_last_step": s1["density_passes"],
                        "batched_fallbacks_last_step": s1["batched_fallbacks"],
                        "fallback_causes_last_step": s1["fallback_causes"],
+                       "tier2_groups_last_step": s1["tier2_groups"],
+                       "tier3_entries_last_step": s1["tier3_entries"],
                        "stage_max": [s1["stage_max_density"], s1["stage_max_force"]],
                        "direct_warps_last_step": [s1["direct_list_warps"],
                                                   s1["direct_stage_warps"]],

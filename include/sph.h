@@ -136,11 +136,18 @@ typedef struct {
   int32_t direct_list_warps;
   int32_t direct_stage_warps;
   /* Particles of the last sph_density + sph_force that the batched kernels
-   * left to the per-pass form, by cause: [0] density group stage overflowed
-   * (both tiers), [1] a density h grew beyond the staged radius, [2] an h not
-   * converged in max_iter passes, [3] force group stage overflowed, [4] / [5]
-   * density / force group task slots overflowed. */
-  int32_t fallback_causes[6];
+   * left to the per-pass form, by cause: [0] density, third-tier walk
+   * frontier overflowed or h outgrew the top-cell width, [1] density, h not
+   * converged in max_iter passes, [2] force, third-tier walk frontier
+   * overflowed, [3] zero. */
+  int32_t fallback_causes[4];
+  /* Batched form, last sph_density + sph_force ([0] density, [1] force):
+   * groups whose stage overflowed and that the second tier staged again by
+   * each target's own radius, and (group, warp) entries whose targets the
+   * third tier computed one warp per target (stage or task-slot overflow, or
+   * an h beyond the staged radius). */
+  int32_t tier2_groups[2];
+  int32_t tier3_entries[2];
   int64_t sort_launches;      /* pair-axis sort launches (cumulative since sph_create) */
 } sph_stats_t;
 

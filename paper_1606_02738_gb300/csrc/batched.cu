@@ -230,113 +230,166 @@ void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s) {
 // written, in walk order, straight into the group's task slots, passing
 // inner nodes put their 8 children on the next frontier. Radius: for the
 // density, min(skin hmax_G, top-cell width); for the force, max(hmax_G,
-// hmax_S). count[g] > tcap marks an overflow (the group is then left to the
-// per-pass form).
+// hmax_S), both from the group's bounding box. A group whose walk overflows
+// (more than tcap leaves, or a frontier beyond kFront) is queued, and the
+// second, tight walk tests every node against each target's own sphere
+// instead (density: min(skin h_i, top-cell width); force: max(h_i, hmax_S)):
+// a group of large-h particles next to a dense clump keeps only what its
+// particles reach. count[g] > tcap still marks an overflow (the group is then
+// left to the per-pass form).
 constexpr int kWalkWarps = 4;
 constexpr int kFront = 512;
 
-__global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a) {
+__global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a, int tight) {
   __shared__ int2 front_all[kWalkWarps][2][kFront];  // (node, neighbour code 0..26)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ltmask = (1u << lane) - 1u;
-  const int g = blockIdx.x * kWalkWarps + warp;
-  if (g >= a.n_groups) return;  // warp-uniform
-  int2 *cur = front_all[warp][0], *nxt = front_all[warp][1];
-  const Group G = a.groups[g];
-  const BoxDev &B = a.boxes[G.box];
-  int c[3];
-  cell_xyz(B, G.cell - B.cell_base, c);
-  const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
-  const float capG = a.force ? G.hmax : fminf(G.hmax * a.skin, wmin);
-  Task *out = a.tasks + (size_t)g * a.tcap;
-
-  // frontier 0: the 27 neighbouring top cells
-  int n = 0;
-  {
-    bool in = lane < 27;
-    int2 e = make_int2(0, lane);
-    if (in) {
-      const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
-      const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
-                         (c[2] + dz + B.n[2]) % B.n[2]};
-      e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+  const int ng = tight ? *a.walk_queued : a.n_groups;
+  for (int q = blockIdx.x * kWalkWarps + warp; q < ng; q += gridDim.x * kWalkWarps) {
+    const int g = tight ? a.walk_queue[q] : q;
+    int2 *cur = front_all[warp][0], *nxt = front_all[warp][1];
+    const Group G = a.groups[g];
+    const BoxDev &B = a.boxes[G.box];
+    int c[3];
+    cell_xyz(B, G.cell - B.cell_base, c);
+    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
+    const float capG = a.force ? G.hmax : fminf(G.hmax * a.skin, wmin);
+    Task *out = a.tasks + (size_t)g * a.tcap;
+    // tight walk: this lane's target (top-cell-relative position, radius)
+    float tx = 0.f, ty = 0.f, tz = 0.f, tr = -1.f;
+    if (tight && lane < G.count) {
+      const int i = G.start + lane;
+      const Leaf &L = a.leaves[a.leaf_of[i]];
+      const float4 p = a.pm[i];
+      tx = (float)(L.o[0] + (double)p.x);
+      ty = (float)(L.o[1] + (double)p.y);
+      tz = (float)(L.o[2] + (double)p.z);
+      const float h = a.hf[i];
+      tr = a.force ? h : fminf(h * a.skin, wmin);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (in) cur[__popc(m & ltmask)] = e;
-    n = __popc(m);
-  }
-  __syncwarp();
-  int ntask = 0;
-  bool overflow = false;
-  while (n > 0) {
-    int nn = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int idx = base + lane;
-      bool leaf_in = false, inner_in = false;
-      int node = 0, code = 0, child = 0, leaf = 0;
-      if (idx < n) {
-        const int2 e = cur[idx];
-        node = e.x;
-        code = e.y;
-        const Node &S = a.nodes[node];
-        if (S.count > 0) {
-          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-          const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
+
+    // frontier 0: the 27 neighbouring top cells
+    int n = 0;
+    {
+      bool in = lane < 27;
+      int2 e = make_int2(0, lane);
+      if (in) {
+        const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+        const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                           (c[2] + dz + B.n[2]) % B.n[2]};
+        e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) cur[__popc(m & ltmask)] = e;
+      n = __popc(m);
+    }
+    __syncwarp();
+    int ntask = 0;
+    bool overflow = false;
+    while (n > 0) {
+      int nn = 0;
+      for (int base = 0; base < n; base += 32) {
+        const int idx = base + lane;
+        bool valid = false;
+        int code = 0, child = 0, leaf = 0;
+        float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f}, shm = 0.f;
+        if (idx < n) {
+          const int2 e = cur[idx];
+          code = e.y;
+          const Node &S = a.nodes[e.x];
+          if (S.count > 0) {
+            const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+            const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]),
+                                 (float)(dz * B.w[2])};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              lo[d] = S.lo[d] + sh[d];
+              hi[d] = S.hi[d] + sh[d];
+            }
+            shm = S.hmax;
+            child = S.child;
+            leaf = S.leaf;
+            valid = true;
+          }
+        }
+        bool pass = false;
+        if (!tight) {
           float d2 = 0.f;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float gap =
-                fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - G.thi[d], G.tlo[d] - S.hi[d] - sh[d]));
+            const float gap = fmaxf(0.f, fmaxf(lo[d] - G.thi[d], G.tlo[d] - hi[d]));
             d2 = fmaf(gap, gap, d2);
           }
-          const float crit = (a.force ? fmaxf(capG, S.hmax) : capG) + B.eps;
-          if (d2 < crit * crit) {
-            child = S.child;
-            leaf = S.leaf;
-            leaf_in = child < 0;
-            inner_in = child >= 0;
+          const float crit = (a.force ? fmaxf(capG, shm) : capG) + B.eps;
+          pass = valid && d2 < crit * crit;
+        } else {
+          for (int k = 0; k < G.count; ++k) {  // warp-uniform loop over the targets
+            const float xk = __shfl_sync(0xffffffffu, tx, k);
+            const float yk = __shfl_sync(0xffffffffu, ty, k);
+            const float zk = __shfl_sync(0xffffffffu, tz, k);
+            const float rk = __shfl_sync(0xffffffffu, tr, k);
+            const float gx = fmaxf(0.f, fmaxf(lo[0] - xk, xk - hi[0]));
+            const float gy = fmaxf(0.f, fmaxf(lo[1] - yk, yk - hi[1]));
+            const float gz = fmaxf(0.f, fmaxf(lo[2] - zk, zk - hi[2]));
+            const float crit = (a.force ? fmaxf(rk, shm) : rk) + B.eps;
+            pass |= fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < crit * crit;
+          }
+          pass = pass && valid;
+        }
+        const bool leaf_in = pass && child < 0, inner_in = pass && child >= 0;
+        const unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
+        if (leaf_in) {
+          const int pos = ntask + __popc(ml & ltmask);
+          if (pos < a.tcap) {
+            const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+            const Leaf &LS = a.leaves[leaf];
+            Task tk;
+            tk.sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
+            tk.sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
+            tk.sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
+            tk.src = leaf;
+            out[pos] = tk;
           }
         }
-      }
-      const unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
-      if (leaf_in) {
-        const int pos = ntask + __popc(ml & ltmask);
-        if (pos < a.tcap) {
-          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-          const Leaf &LS = a.leaves[leaf];
-          Task tk;
-          tk.sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
-          tk.sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
-          tk.sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
-          tk.src = leaf;
-          out[pos] = tk;
+        ntask += __popc(ml);
+        const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
+        if (inner_in) {
+          const int pos = nn + 8 * __popc(mi & ltmask);
+          for (int o = 0; o < 8; ++o)
+            if (pos + o < kFront) nxt[pos + o] = make_int2(child + o, code);
         }
+        nn += 8 * __popc(mi);
       }
-      ntask += __popc(ml);
-      const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
-      if (inner_in) {
-        const int pos = nn + 8 * __popc(mi & ltmask);
-        for (int o = 0; o < 8; ++o)
-          if (pos + o < kFront) nxt[pos + o] = make_int2(child + o, code);
+      __syncwarp();
+      if (nn > kFront) {
+        overflow = true;
+        break;
       }
-      nn += 8 * __popc(mi);
+      int2 *t = cur;
+      cur = nxt;
+      nxt = t;
+      n = nn;
     }
-    __syncwarp();
-    if (nn > kFront) {
-      overflow = true;
-      break;
+    __syncwarp();  // the frontier buffers are reused by this warp's next group
+    overflow = overflow || ntask > a.tcap;
+    if (lane == 0) {
+      a.count[g] = overflow ? a.tcap + 1 : ntask;
+      if (overflow && !tight && a.walk_queue) a.walk_queue[atomicAdd(a.walk_queued, 1)] = g;
     }
-    int2 *t = cur;
-    cur = nxt;
-    nxt = t;
-    n = nn;
   }
-  if (lane == 0) a.count[g] = overflow ? a.tcap + 1 : ntask;
 }
 
+// The walk over every group, then the tight walk over the groups it queued
+// (`*a.walk_queued` must be zero on entry; the second launch reads it on the
+// device).
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  k_group_walk<<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a);
+  k_group_walk<<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a, 0);
+  note_launch();
+  if (!a.walk_queue) return;
+  const int blocks = a.n_groups < 152 * 8 * kWalkWarps ? (a.n_groups + kWalkWarps - 1) / kWalkWarps
+                                                       : 152 * 8;
+  k_group_walk<<<blocks, kWalkWarps * 32, 0, s>>>(a, 1);
   note_launch();
 }
 
@@ -364,6 +417,7 @@ constexpr int kLane = 32;        // list entries per lane
 
 template <int NS>
 struct DensSmem {
+  float4 tgt[32];                           // tight stage: target position (group frame), radius
   float4 stage[NS];                         // position in the group frame, m
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][kLane * 32];     // [entry][lane]
@@ -372,6 +426,7 @@ struct DensSmem {
 
 template <int NS>
 struct ForceSmem {
+  float4 tgt[32];                           // tight stage: target position (group frame), h
   float4 sq[NS];                            // position in the group frame, m
   float2 sf[NS];                            // A (8/pi) h^-4, h^2
   int sj[NS];                               // particle index (velocity read on use)
@@ -425,7 +480,7 @@ template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
                                   float4 *sq, float2 *sf, int *sj, int *wcount,
-                                  unsigned char *tmap, int cap) {
+                                  unsigned char *tmap, int cap, const float4 *tgt) {
   const unsigned ltmask = (1u << lane) - 1u;
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
@@ -499,11 +554,20 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
         const int f = f0 + 32 * u + lane;
         bool in = false;
         if (f < total) {
-          const float R = FORCE ? fmaxf(Rg, fj[u].x) : Rg;
-          const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q[u].x, q[u].x - G.fhi[0]));
-          const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q[u].y, q[u].y - G.fhi[1]));
-          const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q[u].z, q[u].z - G.fhi[2]));
-          in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+          if (!tgt) {
+            const float R = FORCE ? fmaxf(Rg, fj[u].x) : Rg;
+            const float gx = fmaxf(0.f, fmaxf(G.flo[0] - q[u].x, q[u].x - G.fhi[0]));
+            const float gy = fmaxf(0.f, fmaxf(G.flo[1] - q[u].y, q[u].y - G.fhi[1]));
+            const float gz = fmaxf(0.f, fmaxf(G.flo[2] - q[u].z, q[u].z - G.fhi[2]));
+            in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+          } else {  // tight: within some target's own radius (force: max(h_i, h_j))
+            for (int k = 0; k < G.count; ++k) {
+              const float4 t = tgt[k];
+              const float dx = q[u].x - t.x, dy = q[u].y - t.y, dz = q[u].z - t.z;
+              const float R = FORCE ? fmaxf(t.w, fj[u].x) : t.w;
+              in |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R;
+            }
+          }
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
         const int pos = nst + __popc(m & ltmask);
@@ -628,13 +692,13 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
+  constexpr bool TIGHT = NS != kStageD;  // the second tier stages by each target's radius
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int fallback = 0, max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
-  int why[4] = {0, 0, 0, 0};  // fallbacks: stage overflow, h beyond the stage, passes, tasks
+  int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -646,18 +710,29 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
+    if (TIGHT) __syncthreads();  // the previous group's warps are done reading tgt
+    if (TIGHT && threadIdx.x < 32) {  // tight stage: each target's own radius
+      float4 t = make_float4(0.f, 0.f, 0.f, -1.f);
+      if ((int)threadIdx.x < G.count) {
+        const int it = G.start + threadIdx.x;
+        const Leaf &L = a.leaves[a.leaf_of[it]];
+        const float4 pq = a.pm[it];
+        t = make_float4(pq.x + (float)(L.o[0] - G.o[0]), pq.y + (float)(L.o[1] - G.o[1]),
+                        pq.z + (float)(L.o[2] - G.o[2]),
+                        fminf((float)a.h[it] * a.skin_stage, wmin));
+      }
+      S.tgt[threadIdx.x] = t;  // read after stage_group's opening barrier
+    }
     const StageRange sr =
         stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane, Rg, S.stage,
-                           nullptr, nullptr, S.wcount, (unsigned char *)cand, NS);
+                           nullptr, nullptr, S.wcount, (unsigned char *)cand, NS,
+                           TIGHT ? S.tgt : nullptr);
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
-      if (tier == 0 && nt <= a.tcap && sr.maxw <= kBigStageD / kNW) {
-        if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[0], 1)] = g;
-        continue;  // the second tier stages it whole
-      }
-      // the group goes to the per-pass form
-      if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback, ++why[nt > a.tcap ? 3 : 0];
+      if (threadIdx.x < kNW && (TIGHT || nt > a.tcap))  // the third tier walks its targets
+        a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + threadIdx.x;
+      else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap)  // second tier: tight stage
+        a.queue[atomicAdd(&a.ctr->queued[0], 1)] = g;
       continue;
     }
     // this warp's targets: lane = target * kSlice + slice
@@ -760,7 +835,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
           need_list = true;
         }
       }
-      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rg)) {
+      const float Rown = TIGHT && has ? S.tgt[tloc].w : Rg;  // this target's staged radius
+      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rown)) {
         failed = true;  // beyond the staged radius
         break;
       }
@@ -768,10 +844,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     }
     if (lane == 0 && mode) ++n_direct[mode - 1];
     if (failed || !__all_sync(0xffffffffu, fin)) {
-      if (has && slice == 0) {  // left to the per-pass form
-        ++fallback;
-        ++why[failed ? 1 : 2];
-      }
+      // this warp's unfinished targets go to the third tier (done is not set)
+      if (lane == 0) a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + warp;
       continue;
     }
     if (has && slice == 0) {
@@ -794,9 +868,245 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
   }
   ntest = warp_sum(ntest);
   inter = warp_sum(inter);
+  max_it = warp_max_int(max_it);
+  for (int o = 16; o; o >>= 1) st_bits |= __shfl_xor_sync(0xffffffffu, st_bits, o);
+  if (lane == 0) {
+    if (ntest) atomicAdd(&a.ctr->dens_cand, ntest);
+    if (inter) atomicAdd(&a.ctr->dens_inter, inter);
+    if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
+    if (st_bits) atomicOr(&a.ctr->status, st_bits);
+    atomicMax(&a.ctr->stage_max[0], stage_max);
+    if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
+    if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
+  }
+}
+
+// ---------------------------------------------------------------- third tier
+//
+// Targets whose group outgrew both stages or its task slots (a large-h
+// particle beside a dense clump can have thousands of particles inside its h
+// while its weighted neighbour number is 48), or whose h outgrew the staged
+// radius, are done one warp per target: the warp walks the octrees of the 27
+// neighbouring top cells with the target's own sphere and streams the
+// particles of every leaf it reaches from global memory (kU loads in flight
+// per lane), reducing its lanes' partial sums by shuffles in fixed order. No
+// stage and no task slots, so no capacity limit but the frontier's.
+
+constexpr int kSWarps = 4;     // warps per third-tier block
+constexpr int kSFront = 512;   // frontier entries per warp
+
+// Calls f(q, j) for every particle j (q: position shifted into the group
+// frame, mass) of every leaf whose box lies within reach of the point xt
+// (top-cell-relative): reach = R, or max(R, hmax_S) when FORCE. Returns false
+// if the frontier overflowed (the sums are then incomplete).
+template <bool FORCE, class F>
+__device__ bool walk_stream(const Node *nodes, const Leaf *leaves, const float4 *pm,
+                            const BoxDev &B, const Group &G, const float xt[3], float R,
+                            int lane, int2 *cur, int2 *nxt, F &&f) {
+  const unsigned ltmask = (1u << lane) - 1u;
+  int c[3];
+  cell_xyz(B, G.cell - B.cell_base, c);
+  int n = 0;
+  {
+    const bool in = lane < 27;
+    int2 e = make_int2(0, lane);
+    if (in) {
+      const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+      const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                         (c[2] + dz + B.n[2]) % B.n[2]};
+      e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) cur[__popc(m & ltmask)] = e;
+    n = __popc(m);
+  }
+  __syncwarp();
+  bool ok = true;
+  while (n > 0) {
+    int nn = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int idx = base + lane;
+      bool leaf_in = false, inner_in = false;
+      int code = 0, child = 0, leaf = 0;
+      if (idx < n) {
+        const int2 e = cur[idx];
+        code = e.y;
+        const Node &S = nodes[e.x];
+        if (S.count > 0) {
+          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+          const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
+          float d2 = 0.f;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float gap = fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - xt[d], xt[d] - S.hi[d] - sh[d]));
+            d2 = fmaf(gap, gap, d2);
+          }
+          const float crit = (FORCE ? fmaxf(R, S.hmax) : R) + B.eps;
+          if (d2 < crit * crit) {
+            child = S.child;
+            leaf = S.leaf;
+            leaf_in = child < 0;
+            inner_in = child >= 0;
+          }
+        }
+      }
+      // stream the passing leaves, one at a time, all lanes on its particles
+      unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
+      while (ml) {
+        const int src = __ffs(ml) - 1;
+        ml &= ml - 1;
+        const int lf = __shfl_sync(0xffffffffu, leaf, src);
+        const int cd = __shfl_sync(0xffffffffu, code, src);
+        const Leaf &LS = leaves[lf];
+        const int dx = cd / 9 - 1, dy = (cd / 3) % 3 - 1, dz = cd % 3 - 1;
+        const float sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
+        const float sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
+        const float sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
+        for (int k = lane; k < LS.count; k += 32) {
+          const int j = LS.start + k;
+          float4 q = pm[j];
+          q.x += sx;
+          q.y += sy;
+          q.z += sz;
+          f(q, j);
+        }
+      }
+      const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
+      if (inner_in) {
+        const int pos = nn + 8 * __popc(mi & ltmask);
+        for (int o = 0; o < 8; ++o)
+          if (pos + o < kSFront) nxt[pos + o] = make_int2(child + o, code);
+      }
+      nn += 8 * __popc(mi);
+    }
+    __syncwarp();
+    if (nn > kSFront) {
+      ok = false;
+      break;
+    }
+    int2 *t = cur;
+    cur = nxt;
+    nxt = t;
+    n = nn;
+  }
+  __syncwarp();
+  return ok;
+}
+
+// Warp-wide sum in fixed (xor-tree) order: every lane gets the same total.
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Top-cell-relative position of particle i and its position in the group frame.
+__device__ __forceinline__ void target_pos(const Leaf *leaves, const int *leaf_of,
+                                           const float4 *pm, const Group &G, int i, float xt[3],
+                                           float p[3]) {
+  const Leaf &L = leaves[leaf_of[i]];
+  const float4 q = pm[i];
+  const float qq[3] = {q.x, q.y, q.z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xt[d] = (float)(L.o[d] + (double)qq[d]);
+    p[d] = qq[d] + (float)(L.o[d] - G.o[d]);
+  }
+}
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a) {
+  __shared__ int2 front[kSWarps][2][kSFront];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nq = a.ctr->queued2[0];
+  unsigned long long ntest = 0, inter = 0;
+  int fallback = 0, max_it = 0, st_bits = 0;
+  int why[2] = {0, 0};
+  for (int e = blockIdx.x * kSWarps + warp; e < nq * kSub; e += gridDim.x * kSWarps) {
+    const int code = a.queue2[e / kSub];
+    const int g = code / kNW, tloc = (code % kNW) * kSub + e % kSub;
+    const Group G = a.groups[g];
+    if (tloc >= G.count) continue;
+    const int i = G.start + tloc;
+    if (a.done[i]) continue;  // finished by an earlier tier
+    const BoxDev &B = a.boxes[G.box];
+    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
+    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    float xt[3], p[3];
+    target_pos(a.leaves, a.leaf_of, a.pm, G, i, xt, p);
+    HIter it;
+    it.h = a.h[i];
+    it.lo = 0.0;
+    it.hi = 1e308;
+    it.fprev = __int_as_float(0x7f800000);
+    bool fin = false, failed = false;
+    int passes = 0, ngb = 0;
+    float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pass = 0; pass < a.max_iter; ++pass) {
+      const float hf = (float)it.h;
+      if (hf > wmin) {  // the 27 neighbouring top cells no longer cover h
+        failed = true;
+        break;
+      }
+      const float h2 = hf * hf, hinv = 1.f / hf;
+      DensAcc<KAHAN> acc;
+      int seen = 0;
+      const bool ok = walk_stream<false>(a.nodes, a.leaves, a.pm, B, G, xt, hf, lane,
+                                         front[warp][0], front[warp][1], [&](float4 q, int) {
+                                           acc.add(q, p[0], p[1], p[2], h2, hinv);
+                                           ++seen;
+                                         });
+      ntest += seen;
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      const float4 tot = make_float4(warp_sum_f(acc.sw), warp_sum_f(acc.sdw),
+                                     warp_sum_f(acc.smw), warp_sum_f(acc.smdh));
+      int ctot = acc.c;
+      for (int o = 16; o; o >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, o);
+      ++passes;
+      int st = 0;
+      const bool conv = h_newton_step(it, tot.x, tot.y, a.n_ngb, a.tol, hcap, &st);
+      st_bits |= st;
+      if (conv) {
+        fin = true;
+        fs = tot;
+        ngb = ctot - 1;
+        break;
+      }
+    }
+    if (!fin) {  // left to the per-pass form
+      if (lane == 0) {
+        ++fallback;
+        ++why[failed ? 0 : 1];
+      }
+      continue;
+    }
+    if (lane == 0) {
+      float rho, omega, P;
+      float4 fi;
+      if (!finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi))
+        st_bits |= kErrNonPhysical;
+      a.h[i] = it.h;
+      a.hf[i] = (float)it.h;
+      a.rho[i] = rho;
+      a.omega[i] = omega;
+      a.P[i] = P;
+      a.fi[i] = fi;
+      a.nngb[i] = ngb;
+      a.niter[i] = passes;
+      a.done[i] = 1;
+      inter += (unsigned long long)ngb;
+      max_it = max(max_it, passes);
+    }
+  }
+  ntest = warp_sum(ntest);
+  inter = warp_sum(inter);
   fallback = (int)warp_sum((unsigned long long)fallback);
   max_it = warp_max_int(max_it);
   for (int o = 16; o; o >>= 1) st_bits |= __shfl_xor_sync(0xffffffffu, st_bits, o);
+  const int w1 = (int)warp_sum((unsigned long long)why[0]);
+  const int w2 = (int)warp_sum((unsigned long long)why[1]);
   if (lane == 0) {
     if (ntest) atomicAdd(&a.ctr->dens_cand, ntest);
     if (inter) atomicAdd(&a.ctr->dens_inter, inter);
@@ -804,15 +1114,81 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
       atomicAdd(&a.ctr->unconverged, fallback);
       atomicAdd(&a.ctr->fallback, fallback);
     }
+    if (w1) atomicAdd(&a.ctr->why[0], w1);
+    if (w2) atomicAdd(&a.ctr->why[1], w2);
     if (max_it) atomicMax(&a.ctr->max_iter_used, max_it);
     if (st_bits) atomicOr(&a.ctr->status, st_bits);
-    atomicMax(&a.ctr->stage_max[0], stage_max);
-    if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
-    if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
-  for (int k = 0; k < 4; ++k) {
-    const int w = (int)warp_sum((unsigned long long)why[k]);
-    if (lane == 0 && w) atomicAdd(&a.ctr->why[k == 3 ? 4 : k], w);
+}
+
+__global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a) {
+  __shared__ int2 front[kSWarps][2][kSFront];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nq = a.ctr->queued2[1];
+  unsigned long long ntest = 0, inter = 0;
+  int fallback = 0;
+  for (int e = blockIdx.x * kSWarps + warp; e < nq * kSub; e += gridDim.x * kSWarps) {
+    const int code = a.queue2[e / kSub];
+    const int g = code / kNW, tloc = (code % kNW) * kSub + e % kSub;
+    const Group G = a.groups[g];
+    if (tloc >= G.count) continue;
+    const int i = G.start + tloc;
+    const BoxDev &B = a.boxes[G.box];
+    float xt[3], p[3];
+    target_pos(a.leaves, a.leaf_of, a.pm, G, i, xt, p);
+    const float4 fi = a.fi[i], vi = a.vu[i];
+    float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+    int c = 0, seen = 0;
+    const bool ok = walk_stream<true>(
+        a.nodes, a.leaves, a.pm, B, G, xt, fi.x, lane, front[warp][0], front[warp][1],
+        [&](float4 q, int j) {
+          ++seen;
+          const float dx = p[0] - q.x, dy = p[1] - q.y, dz = p[2] - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (!(r2 > 0.f)) return;
+          const float4 fj = a.fi[j];
+          if (!(r2 < fmaxf(fi.w, fj.w))) return;
+          const float rinv = rsqrtf(r2);
+          const float r = r2 * rinv;
+          const float ti = fi.z * dw_only(r * fi.y);  // A_i dW/dr(r, h_i)
+          const float tj = fj.z * dw_only(r * fj.y);  // A_j dW/dr(r, h_j)
+          const float fac = q.w * (ti + tj) * rinv;
+          const float4 vj = a.vu[j];
+          const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+          ax = fmaf(-fac, dx, ax);
+          ay = fmaf(-fac, dy, ay);
+          az = fmaf(-fac, dz, az);
+          du = fmaf(q.w * ti * rinv, dvdx, du);
+          ++c;
+        });
+    ntest += seen;
+    if (!ok) {  // left to the per-pass form
+      if (lane == 0) ++fallback;
+      continue;
+    }
+    ax = warp_sum_f(ax);
+    ay = warp_sum_f(ay);
+    az = warp_sum_f(az);
+    du = warp_sum_f(du);
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      a.acc[i] = make_float4(ax, ay, az, du);
+      a.nforce[i] = c;
+      a.fdone[i] = 1;
+      inter += (unsigned long long)c;
+    }
+  }
+  ntest = warp_sum(ntest);
+  inter = warp_sum(inter);
+  fallback = (int)warp_sum((unsigned long long)fallback);
+  if (lane == 0) {
+    if (ntest) atomicAdd(&a.ctr->force_cand, ntest);
+    if (inter) atomicAdd(&a.ctr->force_inter, inter);
+    if (fallback) {
+      atomicAdd(&a.ctr->unconverged, fallback);
+      atomicAdd(&a.ctr->fallback, fallback);
+      atomicAdd(&a.ctr->why[2], fallback);
+    }
   }
 }
 
@@ -839,10 +1215,13 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   if (a.kahan) {
     launch_density_tier<true, kStageD>(a, 0, blocks, s);
     launch_density_tier<true, kBigStageD>(a, 1, big, s);
+    k_density_stream<true><<<152 * 8, 128, 0, s>>>(a);
   } else {
     launch_density_tier<false, kStageD>(a, 0, blocks, s);
     launch_density_tier<false, kBigStageD>(a, 1, big, s);
+    k_density_stream<false><<<152 * 8, 128, 0, s>>>(a);
   }
+  note_launch();
 }
 
 // One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
@@ -879,13 +1258,13 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
+  constexpr bool TIGHT = NS != kStageF;  // the second tier stages by each target's radius
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int fallback = 0, stage_max = 0, n_direct[2] = {0, 0};
-  int why0 = 0, why1 = 0;  // fallbacks for stage overflow, for task overflow
+  int stage_max = 0, n_direct[2] = {0, 0};
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -893,17 +1272,28 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
+    if (TIGHT) __syncthreads();  // the previous group's warps are done with the smem
+    if (TIGHT && threadIdx.x < 32) {  // tight stage: each target's own h
+      float4 t = make_float4(0.f, 0.f, 0.f, -1.f);
+      if ((int)threadIdx.x < G.count) {
+        const int it = G.start + threadIdx.x;
+        const Leaf &L = a.leaves[a.leaf_of[it]];
+        const float4 pq = a.pm[it];
+        t = make_float4(pq.x + (float)(L.o[0] - G.o[0]), pq.y + (float)(L.o[1] - G.o[1]),
+                        pq.z + (float)(L.o[2] - G.o[2]), a.fi[it].x);
+      }
+      S.tgt[threadIdx.x] = t;  // read after stage_group's opening barrier
+    }
     const StageRange sr =
         stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane, G.hmax, S.sq,
-                          S.sf, S.sj, S.wcount, (unsigned char *)cand, NS);
+                          S.sf, S.sj, S.wcount, (unsigned char *)cand, NS,
+                          TIGHT ? S.tgt : nullptr);
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
-      if (tier == 0 && nt <= a.tcap && sr.maxw <= kBigStageF / kNW) {
-        if (threadIdx.x == 0) a.queue[atomicAdd(&a.ctr->queued[1], 1)] = g;
-        continue;  // the second tier stages it whole
-      }
-      if (lane < G.count - warp * kSub && (lane & (kSlice - 1)) == 0 && lane < kSub * kSlice)
-        ++fallback, ++(nt > a.tcap ? why1 : why0);
+      if (threadIdx.x < kNW && (TIGHT || nt > a.tcap))  // the third tier walks its targets
+        a.queue2[atomicAdd(&a.ctr->queued2[1], 1)] = g * kNW + threadIdx.x;
+      else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap)  // second tier: tight stage
+        a.queue[atomicAdd(&a.ctr->queued[1], 1)] = g;
       continue;
     }
     const int tloc = warp * kSub + (lane >> 2);
@@ -981,22 +1371,14 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
   }
   ntest = warp_sum(ntest);
   inter = warp_sum(inter);
-  fallback = (int)warp_sum((unsigned long long)fallback);
   if (lane == 0) {
     if (ntest) atomicAdd(&a.ctr->force_cand, ntest);
     if (inter) atomicAdd(&a.ctr->force_inter, inter);
-    if (fallback) {
-      atomicAdd(&a.ctr->unconverged, fallback);
-      atomicAdd(&a.ctr->fallback, fallback);
-    }
     atomicMax(&a.ctr->stage_max[1], stage_max);
     if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
     if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
-  why0 = (int)warp_sum((unsigned long long)why0);
-  why1 = (int)warp_sum((unsigned long long)why1);
-  if (lane == 0 && why0) atomicAdd(&a.ctr->why[3], why0);
-  if (lane == 0 && why1) atomicAdd(&a.ctr->why[5], why1);
+
 }
 
 template <int NS>
@@ -1017,6 +1399,8 @@ void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
   launch_force_tier<kStageF>(a, 0, blocks, s);
   launch_force_tier<kBigStageF>(a, 1, big, s);
+  k_force_stream<<<152 * 8, 128, 0, s>>>(a);
+  note_launch();
 }
 
 }  // namespace sph

@@ -629,7 +629,7 @@ int build_groups(sph_ctx *c) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->n_groups = ng;
   TRY(ensure(c, c->groups, sizeof(Group) * (size_t)std::max(ng, 1)));
-  TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1) * 5));  // queue, queue2
   ga = group_args(c);
   launch_group_fill(ga, c->stream);
   launch_group_geometry(ga, c->stream);
@@ -658,6 +658,12 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &t
   la.count = as<int>(cnt);
   la.tasks = as<Task>(tasks);
   la.status = &c->ctr->status;
+  la.leaf_of = c->leaf_of;
+  la.pm = c->pm;
+  la.hf = c->hf;
+  la.walk_queue = as<int>(c->gqueue);  // free until the interaction kernels run
+  la.walk_queued = &c->ctr->walk_queued;
+  CUDA_TRY(cudaMemsetAsync(la.walk_queued, 0, sizeof(int), c->stream));
   launch_group_lists(la, c->stream);
   toc(c, kLists);
   return sync_check(c);
@@ -704,7 +710,9 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   da.P = c->P;
   da.fi = c->fi;
   da.ctr = c->ctr;
-  da.queue = as<int>(c->gqueue);  // ctr->queued was zeroed with the counters
+  da.queue = as<int>(c->gqueue);  // ctr->queued, queued2 were zeroed with the counters
+  da.queue2 = as<int>(c->gqueue) + c->n_groups;
+  da.nodes = as<Node>(c->nodes);
   tic(c, kDens);
   launch_density_batched(da, c->stream);
   toc(c, kDens);
@@ -834,6 +842,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->queued2[1], 0, sizeof(int), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
@@ -851,6 +860,9 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   fa.fdone = c->fdone;
   fa.ctr = c->ctr;
   fa.queue = as<int>(c->gqueue);
+  fa.queue2 = as<int>(c->gqueue) + c->n_groups;
+  fa.nodes = as<Node>(c->nodes);
+  fa.boxes = c->boxes_d;
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -1147,7 +1159,11 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->t_sort_ms = c->t_ms[kSort];
   out->direct_list_warps = c->ctr_h->direct[0];
   out->direct_stage_warps = c->ctr_h->direct[1];
-  for (int k = 0; k < 6; ++k) out->fallback_causes[k] = c->ctr_h->why[k];
+  for (int k = 0; k < 4; ++k) out->fallback_causes[k] = c->ctr_h->why[k];
+  for (int k = 0; k < 2; ++k) {
+    out->tier2_groups[k] = c->ctr_h->queued[k];
+    out->tier3_entries[k] = c->ctr_h->queued2[k];
+  }
   out->sort_launches = c->sort_launches;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;

@@ -88,9 +88,11 @@ struct DevCounters {
   int direct[2];                      // batched warp-groups that read their candidates
                                       // directly (a list overflowed) / the whole stage
   int queued[2];                      // groups queued for the second (larger-stage) tier
-  int why[6];                         // batched fallbacks: density stage overflow, density
-                                      // h beyond the stage, density passes, force stage
-                                      // overflow, density / force task-slot overflow
+  int walk_queued;                    // groups queued for the tight walk
+  int queued2[2];                     // (group, warp) entries queued for the third tier
+  int why[4];                         // batched fallbacks: density third-tier walk (frontier
+                                      // or h beyond the top cell), density passes, force
+                                      // third-tier walk, (zero)
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
@@ -471,6 +473,11 @@ struct GroupListArgs {
   int *count;            // [n_groups] tasks found (> tcap: overflow)
   Task *tasks;           // [n_groups * tcap]
   int *status;
+  const int *leaf_of;    // targets of the tight walk
+  const float4 *pm;
+  const float *hf;
+  int *walk_queue;       // [n_groups] groups whose walk overflowed (null: no tight walk)
+  int *walk_queued;      // device count of walk_queue, zero on entry
 };
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
 
@@ -498,6 +505,8 @@ struct BatchDensArgs {
   float4 *fi;
   DevCounters *ctr;
   int *queue;            // [n_groups] groups handed to the second tier
+  int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
+  const Node *nodes;     // the third tier walks the octrees itself
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 
@@ -517,6 +526,9 @@ struct BatchForceArgs {
   unsigned char *fdone;  // per particle: force written by the batched kernel
   DevCounters *ctr;
   int *queue;            // [n_groups] groups handed to the second tier
+  int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
+  const Node *nodes;     // the third tier walks the octrees itself
+  const BoxDev *boxes;
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 

@@ -68,7 +68,8 @@ class sph_stats_t(ctypes.Structure):
                 ("t_force_ms", ctypes.c_double), ("t_integrate_ms", ctypes.c_double),
                 ("t_sort_ms", ctypes.c_double),
                 ("direct_list_warps", ctypes.c_int32), ("direct_stage_warps", ctypes.c_int32),
-                ("fallback_causes", ctypes.c_int32 * 6), ("sort_launches", ctypes.c_int64)]
+                ("fallback_causes", ctypes.c_int32 * 4),
+                ("tier2_groups", ctypes.c_int32 * 2), ("tier3_entries", ctypes.c_int32 * 2), ("sort_launches", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):
