@@ -892,102 +892,97 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
 // per lane), reducing its lanes' partial sums by shuffles in fixed order. No
 // stage and no task slots, so no capacity limit but the frontier's.
 
-constexpr int kSWarps = 4;     // warps per third-tier block
-constexpr int kSFront = 512;   // frontier entries per warp
+constexpr int kSWarps = 4;       // warps per third-tier block
+constexpr int kSStack = 1536;    // node stack entries per warp
 
 // Calls f(q, j) for every particle j (q: position shifted into the group
 // frame, mass) of every leaf whose box lies within reach of the point xt
-// (top-cell-relative): reach = R, or max(R, hmax_S) when FORCE. Returns false
-// if the frontier overflowed (the sums are then incomplete).
+// (top-cell-relative): reach = R, or max(R, hmax_S) when FORCE. The walk is
+// depth first with a warp-wide stack: each round pops up to 32 nodes (fewer
+// when the stack is nearly full, so 8 children per popped node always fit),
+// streams the passing leaves and pushes the passing inner nodes' children.
+// Deterministic order. Returns false if the stack overflowed anyway (the
+// sums are then incomplete).
 template <bool FORCE, class F>
 __device__ bool walk_stream(const Node *nodes, const Leaf *leaves, const float4 *pm,
                             const BoxDev &B, const Group &G, const float xt[3], float R,
-                            int lane, int2 *cur, int2 *nxt, F &&f) {
+                            int lane, int2 *stk, F &&f) {
   const unsigned ltmask = (1u << lane) - 1u;
   int c[3];
   cell_xyz(B, G.cell - B.cell_base, c);
-  int n = 0;
-  {
-    const bool in = lane < 27;
-    int2 e = make_int2(0, lane);
-    if (in) {
-      const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
-      const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
-                         (c[2] + dz + B.n[2]) % B.n[2]};
-      e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (in) cur[__popc(m & ltmask)] = e;
-    n = __popc(m);
+  if (lane < 27) {
+    const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+    const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                       (c[2] + dz + B.n[2]) % B.n[2]};
+    stk[26 - lane] = make_int2(B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2], lane);
   }
   __syncwarp();
+  int n = 27;
   bool ok = true;
   while (n > 0) {
-    int nn = 0;
-    for (int base = 0; base < n; base += 32) {
-      const int idx = base + lane;
-      bool leaf_in = false, inner_in = false;
-      int code = 0, child = 0, leaf = 0;
-      if (idx < n) {
-        const int2 e = cur[idx];
-        code = e.y;
-        const Node &S = nodes[e.x];
-        if (S.count > 0) {
-          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-          const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
-          float d2 = 0.f;
+    int k = min(32, n);
+    const int room = (kSStack - n) / 7;  // pops whose 8 children fit after the pop
+    if (k > room) k = room > 0 ? room : 1;
+    bool leaf_in = false, inner_in = false;
+    int code = 0, child = 0, leaf = 0;
+    if (lane < k) {
+      const int2 e = stk[n - 1 - lane];
+      code = e.y;
+      const Node &S = nodes[e.x];
+      if (S.count > 0) {
+        const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+        const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
+        float d2 = 0.f;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            const float gap = fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - xt[d], xt[d] - S.hi[d] - sh[d]));
-            d2 = fmaf(gap, gap, d2);
-          }
-          const float crit = (FORCE ? fmaxf(R, S.hmax) : R) + B.eps;
-          if (d2 < crit * crit) {
-            child = S.child;
-            leaf = S.leaf;
-            leaf_in = child < 0;
-            inner_in = child >= 0;
-          }
+        for (int d = 0; d < 3; ++d) {
+          const float gap = fmaxf(0.f, fmaxf(S.lo[d] + sh[d] - xt[d], xt[d] - S.hi[d] - sh[d]));
+          d2 = fmaf(gap, gap, d2);
+        }
+        const float crit = (FORCE ? fmaxf(R, S.hmax) : R) + B.eps;
+        if (d2 < crit * crit) {
+          child = S.child;
+          leaf = S.leaf;
+          leaf_in = child < 0;
+          inner_in = child >= 0;
         }
       }
-      // stream the passing leaves, one at a time, all lanes on its particles
-      unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
-      while (ml) {
-        const int src = __ffs(ml) - 1;
-        ml &= ml - 1;
-        const int lf = __shfl_sync(0xffffffffu, leaf, src);
-        const int cd = __shfl_sync(0xffffffffu, code, src);
-        const Leaf &LS = leaves[lf];
-        const int dx = cd / 9 - 1, dy = (cd / 3) % 3 - 1, dz = cd % 3 - 1;
-        const float sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
-        const float sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
-        const float sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
-        for (int k = lane; k < LS.count; k += 32) {
-          const int j = LS.start + k;
-          float4 q = pm[j];
-          q.x += sx;
-          q.y += sy;
-          q.z += sz;
-          f(q, j);
-        }
-      }
-      const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
-      if (inner_in) {
-        const int pos = nn + 8 * __popc(mi & ltmask);
-        for (int o = 0; o < 8; ++o)
-          if (pos + o < kSFront) nxt[pos + o] = make_int2(child + o, code);
-      }
-      nn += 8 * __popc(mi);
     }
     __syncwarp();
-    if (nn > kSFront) {
+    n -= k;
+    // stream the passing leaves, one at a time, all lanes on its particles
+    unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
+    while (ml) {
+      const int src = __ffs(ml) - 1;
+      ml &= ml - 1;
+      const int lf = __shfl_sync(0xffffffffu, leaf, src);
+      const int cd = __shfl_sync(0xffffffffu, code, src);
+      const Leaf &LS = leaves[lf];
+      const int dx = cd / 9 - 1, dy = (cd / 3) % 3 - 1, dz = cd % 3 - 1;
+      const float sx = (float)(LS.o[0] + dx * B.w[0] - G.o[0]);
+      const float sy = (float)(LS.o[1] + dy * B.w[1] - G.o[1]);
+      const float sz = (float)(LS.o[2] + dz * B.w[2] - G.o[2]);
+      for (int kk = lane; kk < LS.count; kk += 32) {
+        const int j = LS.start + kk;
+        float4 q = pm[j];
+        q.x += sx;
+        q.y += sy;
+        q.z += sz;
+        f(q, j);
+      }
+    }
+    // push the children of passing inner nodes (last pushed is popped first)
+    const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
+    if (inner_in) {
+      const int pos = n + 8 * __popc(mi & ltmask);
+      for (int o = 0; o < 8; ++o)
+        if (pos + o < kSStack) stk[pos + o] = make_int2(child + 7 - o, code);
+    }
+    n += 8 * __popc(mi);
+    if (n > kSStack) {
       ok = false;
       break;
     }
-    int2 *t = cur;
-    cur = nxt;
-    nxt = t;
-    n = nn;
+    __syncwarp();
   }
   __syncwarp();
   return ok;
@@ -1015,7 +1010,7 @@ __device__ __forceinline__ void target_pos(const Leaf *leaves, const int *leaf_o
 
 template <bool KAHAN>
 __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a) {
-  __shared__ int2 front[kSWarps][2][kSFront];
+  __shared__ int2 stack[kSWarps][kSStack];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = a.ctr->queued2[0];
   unsigned long long ntest = 0, inter = 0;
@@ -1043,15 +1038,20 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; pass < a.max_iter; ++pass) {
       const float hf = (float)it.h;
-      if (hf > wmin) {  // the 27 neighbouring top cells no longer cover h
-        failed = true;
+      if (hf * (1.f + 1e-6f) > wmin) {  // the 27 neighbouring top cells no longer cover h:
+        failed = true;                   // keep the grown h for the regrid, which the
+        st_bits |= kErrHGrid;            // caller runs before the next attempt
+        if (lane == 0) {
+          a.h[i] = it.h;
+          a.hf[i] = hf;
+        }
         break;
       }
       const float h2 = hf * hf, hinv = 1.f / hf;
       DensAcc<KAHAN> acc;
       int seen = 0;
       const bool ok = walk_stream<false>(a.nodes, a.leaves, a.pm, B, G, xt, hf, lane,
-                                         front[warp][0], front[warp][1], [&](float4 q, int) {
+                                         stack[warp], [&](float4 q, int) {
                                            acc.add(q, p[0], p[1], p[2], h2, hinv);
                                            ++seen;
                                          });
@@ -1122,7 +1122,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
 }
 
 __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a) {
-  __shared__ int2 front[kSWarps][2][kSFront];
+  __shared__ int2 stack[kSWarps][kSStack];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = a.ctr->queued2[1];
   unsigned long long ntest = 0, inter = 0;
@@ -1140,7 +1140,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a)
     float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
     int c = 0, seen = 0;
     const bool ok = walk_stream<true>(
-        a.nodes, a.leaves, a.pm, B, G, xt, fi.x, lane, front[warp][0], front[warp][1],
+        a.nodes, a.leaves, a.pm, B, G, xt, fi.x, lane, stack[warp],
         [&](float4 q, int j) {
           ++seen;
           const float dx = p[0] - q.x, dy = p[1] - q.y, dz = p[2] - q.z;

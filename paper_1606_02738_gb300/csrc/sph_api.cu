@@ -731,7 +731,17 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   c->last_passes = 0;
   c->last_rebuilds = 0;
-  if (c->p.mode == SPH_MODE_BATCHED) TRY(density_batched(c, vu_for_P));
+  if (c->p.mode == SPH_MODE_BATCHED) {
+    TRY(density_batched(c, vu_for_P));
+    for (int r = 0; r < 2 && (c->ctr_h->status & kErrHGrid); ++r) {
+      // some h outgrew its top cell: regrid with the grown h and start again
+      TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+      launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
+      CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+      ++c->last_rebuilds;
+      TRY(density_batched(c, vu_for_P));
+    }
+  }
   const int max_passes = c->p.max_iter + 8;
   for (int pass = 0;; ++pass) {
     if (pass >= max_passes)

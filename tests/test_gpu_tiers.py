@@ -1,0 +1,78 @@
+"""The batched form's three tiers on inputs that need them, through the C ABI
+and against the FP64 oracle.
+
+Tier 1 stages a group of <= 32 particles by its bounding box; a group whose
+stage overflows is staged again by each target's own radius (tier 2); a
+group that overflows that too, or its task slots, or whose h outgrows the
+staged radius, is computed one warp per target by a direct walk of the
+octrees (tier 3). Large h contrast (dense clumps beside sparse background)
+and very large neighbour numbers drive particles into tiers 2 and 3; the
+results must still match the oracle, and nothing may be left to the
+per-pass form.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_02738_gb300 import inputs
+from paper_1606_02738_gb300 import sph
+from _parity import compare_density, compare_force, force_counts_close, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sph.lib()
+
+
+@pytest.mark.parametrize("precision", [sph.SPH_PREC_FP32, sph.SPH_PREC_KAHAN])
+def test_clustered_from_flat_guess_uses_tiers_2_and_3(precision):
+    """A uniform initial h over strong clumps: the first density pushes many
+    groups past their stage (their h shrinks or grows far from the guess)."""
+    p = inputs.clustered(60000, n_spheres=8, seed=11, sigma_v=0.1)
+    g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, precision=precision)
+    s = run_oracle(p)
+    assert s.h.max() / s.h.min() > 20
+    st = g["stats"]
+    assert st["tier2_groups"][0] > 0 and st["tier3_entries"][0] > 0, st
+    assert st["batched_fallbacks"] == 0, st
+    compare_density(g, s)
+    compare_force(g, s)
+    force_counts_close(g, s)
+
+
+def test_clustered_steady_state_second_call():
+    """At converged h (second density + force on the same state) the tiers
+    still give the oracle's values."""
+    p = inputs.clustered(60000, n_spheres=8, seed=12, sigma_v=0.1)
+    c = sph.Context(mode=sph.SPH_MODE_BATCHED).load(p)
+    c.density()
+    c.force()
+    c.density()
+    c.force()
+    st = c.stats()
+    g = {k: c.get(k).cpu().numpy() for k in ("h", "rho", "omega", "P", "a", "dudt", "nngb",
+                                              "nforce")}
+    c.close()
+    s = run_oracle(p)
+    assert st["batched_fallbacks"] == 0, st
+    assert st["tier2_groups"][0] + st["tier2_groups"][1] > 0, st
+    compare_density(g, s)
+    compare_force(g, s)
+
+
+def test_huge_neighbour_number_reaches_tier_3_for_density_and_force():
+    """n_ngb = 2000: the union of a group's 32 spheres holds more particles
+    than the second tier's stage, for the density and for the force."""
+    p = inputs.uniform(40000, seed=331, sigma_v=0.2)
+    p.n_ngb = 2000.0
+    g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, n_ngb=2000.0)
+    s = run_oracle(p)
+    st = g["stats"]
+    assert st["tier3_entries"][0] > 0 and st["tier3_entries"][1] > 0, st
+    assert st["batched_fallbacks"] == 0, st
+    compare_density(g, s)
+    compare_force(g, s)
