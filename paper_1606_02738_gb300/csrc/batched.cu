@@ -182,6 +182,7 @@ __global__ void k_group_geometry(GroupBuildArgs a) {
       flo[d] = fhi[d] = f;
       tlo[d] = thi[d] = t;
     }
+    a.gpos[i] = make_float4(flo[0], flo[1], flo[2], q.w);
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d)
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
     const BoxDev &B = a.boxes[G.box];
     int c[3];
     cell_xyz(B, G.cell - B.cell_base, c);
-    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
+    const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
     const float capG = a.force ? G.hmax : fminf(G.hmax * a.skin, wmin);
     Task *out = a.tasks + (size_t)g * a.tcap;
     // tight walk: this lane's target (top-cell-relative position, radius)
@@ -299,8 +300,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
           const Node &S = a.nodes[e.x];
           if (S.count > 0) {
             const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-            const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]),
-                                 (float)(dz * B.w[2])};
+            const float sh[3] = {dx * B.wf[0], dy * B.wf[1], dz * B.wf[2]};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
               lo[d] = S.lo[d] + sh[d];
@@ -693,6 +693,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
   constexpr bool TIGHT = NS != kStageD;  // the second tier stages by each target's radius
+  const double tol_n = a.tol * a.n_ngb;
+  const float gm1 = (float)(a.gamma - 1.0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
@@ -705,8 +707,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     const int g = tier_group(tier, q, a.queue);
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
-    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
-    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
+    const float hcap = (float)B.hcap;
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
@@ -715,11 +717,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
       float4 t = make_float4(0.f, 0.f, 0.f, -1.f);
       if ((int)threadIdx.x < G.count) {
         const int it = G.start + threadIdx.x;
-        const Leaf &L = a.leaves[a.leaf_of[it]];
-        const float4 pq = a.pm[it];
-        t = make_float4(pq.x + (float)(L.o[0] - G.o[0]), pq.y + (float)(L.o[1] - G.o[1]),
-                        pq.z + (float)(L.o[2] - G.o[2]),
-                        fminf((float)a.h[it] * a.skin_stage, wmin));
+        const float4 pq = a.gpos[it];
+        t = make_float4(pq.x, pq.y, pq.z, fminf(a.hf[it] * a.skin_stage, wmin));
       }
       S.tgt[threadIdx.x] = t;  // read after stage_group's opening barrier
     }
@@ -740,18 +739,13 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     const bool has = tloc < G.count;
     const int i = G.start + tloc;
     float px = 0.f, py = 0.f, pz = 0.f;
-    HIter it;
-    it.h = 1.0;
-    it.lo = 0.0;
-    it.hi = 1e308;
-    it.fprev = __int_as_float(0x7f800000);
+    HIterF it;
+    it.start(has ? a.hf[i] : 1.f);
     if (has) {
-      const Leaf &L = a.leaves[a.leaf_of[i]];
-      const float4 q = a.pm[i];
-      px = q.x + (float)(L.o[0] - G.o[0]);
-      py = q.y + (float)(L.o[1] - G.o[1]);
-      pz = q.z + (float)(L.o[2] - G.o[2]);
-      it.h = a.h[i];
+      const float4 q = a.gpos[i];
+      px = q.x;
+      py = q.y;
+      pz = q.z;
     }
     if (!__any_sync(0xffffffffu, has)) continue;  // this warp has no targets
     float blo[3], bhi[3];
@@ -768,7 +762,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     for (int pass = 0; pass < a.max_iter; ++pass) {
       if (mode < 2 && __any_sync(0xffffffffu, need_filter)) {
         // sub-cluster radius: its largest h x the stage skin, capped by Rg
-        float hm = has && !fin ? (float)it.h : 0.f;
+        float hm = has && !fin ? it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
         rsub = fminf(hm * a.skin_stage, Rg);
         ncand = filter_stage<false>(S.stage, nullptr, sr, blo, bhi, rsub, cand, kCandD, lane);
@@ -779,7 +773,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
       if (mode == 0 && __any_sync(0xffffffffu, need_list)) {
         float rl2 = -1.f;
         if (need_list) {
-          rl = fminf((float)it.h * a.skin_list, rsub);
+          rl = fminf(it.h * a.skin_list, rsub);
           rl2 = rl * rl;
           cnt = 0;
           ntest += (ncand + kSlice - 1 - slice) / kSlice;
@@ -800,7 +794,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
         __syncwarp();
       }
       // partial sums over this lane's slice at the current h
-      const float hf = (float)it.h;
+      const float hf = it.h;
       const float h2 = fin ? -1.f : hf * hf;
       const float hinv = 1.f / hf;
       DensAcc<KAHAN> acc;
@@ -823,20 +817,20 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
       if (!fin) {
         ++passes;
         int st = 0;
-        const bool conv = h_newton_step(it, tot.x, tot.y, a.n_ngb, a.tol, hcap, &st);
+        const bool conv = h_newton_step_f(it, tot.x, tot.y, a.n_ngb, tol_n, hcap, &st);
         st_bits |= st;
         if (conv) {
           fin = true;
           fs = tot;
           ngb = ctot - 1;  // the self term is always inside
-        } else if ((float)it.h > rsub) {
+        } else if (it.h > rsub) {
           need_filter = true;
-        } else if ((float)it.h > rl) {
+        } else if (it.h > rl) {
           need_list = true;
         }
       }
       const float Rown = TIGHT && has ? S.tgt[tloc].w : Rg;  // this target's staged radius
-      if (__any_sync(0xffffffffu, !fin && (float)it.h > Rown)) {
+      if (__any_sync(0xffffffffu, !fin && it.h > Rown)) {
         failed = true;  // beyond the staged radius
         break;
       }
@@ -851,10 +845,10 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     if (has && slice == 0) {
       float rho, omega, P;
       float4 fi;
-      const bool ok = finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi);
+      const bool ok = finalise_density(it.h, fs, a.vu[i].w, gm1, &rho, &omega, &P, &fi);
       if (!ok) st_bits |= kErrNonPhysical;
-      a.h[i] = it.h;
-      a.hf[i] = (float)it.h;
+      a.h[i] = (double)it.h;
+      a.hf[i] = it.h;
       a.rho[i] = rho;
       a.omega[i] = omega;
       a.P[i] = P;
@@ -931,7 +925,7 @@ __device__ bool walk_stream(const Node *nodes, const Leaf *leaves, const float4 
       const Node &S = nodes[e.x];
       if (S.count > 0) {
         const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
-        const float sh[3] = {(float)(dx * B.w[0]), (float)(dy * B.w[1]), (float)(dz * B.w[2])};
+        const float sh[3] = {dx * B.wf[0], dy * B.wf[1], dz * B.wf[2]};
         float d2 = 0.f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1024,25 +1018,22 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
     const int i = G.start + tloc;
     if (a.done[i]) continue;  // finished by an earlier tier
     const BoxDev &B = a.boxes[G.box];
-    const float wmin = (float)fmin(B.w[0], fmin(B.w[1], B.w[2]));
-    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
+    const float hcap = (float)B.hcap;
     float xt[3], p[3];
     target_pos(a.leaves, a.leaf_of, a.pm, G, i, xt, p);
-    HIter it;
-    it.h = a.h[i];
-    it.lo = 0.0;
-    it.hi = 1e308;
-    it.fprev = __int_as_float(0x7f800000);
+    HIterF it;
+    it.start(a.hf[i]);
     bool fin = false, failed = false;
     int passes = 0, ngb = 0;
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; pass < a.max_iter; ++pass) {
-      const float hf = (float)it.h;
+      const float hf = it.h;
       if (hf * (1.f + 1e-6f) > wmin) {  // the 27 neighbouring top cells no longer cover h:
         failed = true;                   // keep the grown h for the regrid, which the
         st_bits |= kErrHGrid;            // caller runs before the next attempt
         if (lane == 0) {
-          a.h[i] = it.h;
+          a.h[i] = (double)hf;
           a.hf[i] = hf;
         }
         break;
@@ -1066,7 +1057,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
       for (int o = 16; o; o >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, o);
       ++passes;
       int st = 0;
-      const bool conv = h_newton_step(it, tot.x, tot.y, a.n_ngb, a.tol, hcap, &st);
+      const bool conv = h_newton_step_f(it, tot.x, tot.y, a.n_ngb, a.tol * a.n_ngb, hcap, &st);
       st_bits |= st;
       if (conv) {
         fin = true;
@@ -1085,10 +1076,10 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
     if (lane == 0) {
       float rho, omega, P;
       float4 fi;
-      if (!finalise_density(it.h, fs, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi))
+      if (!finalise_density(it.h, fs, a.vu[i].w, (float)(a.gamma - 1.0), &rho, &omega, &P, &fi))
         st_bits |= kErrNonPhysical;
-      a.h[i] = it.h;
-      a.hf[i] = (float)it.h;
+      a.h[i] = (double)it.h;
+      a.hf[i] = it.h;
       a.rho[i] = rho;
       a.omega[i] = omega;
       a.P[i] = P;
@@ -1277,10 +1268,8 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
       float4 t = make_float4(0.f, 0.f, 0.f, -1.f);
       if ((int)threadIdx.x < G.count) {
         const int it = G.start + threadIdx.x;
-        const Leaf &L = a.leaves[a.leaf_of[it]];
-        const float4 pq = a.pm[it];
-        t = make_float4(pq.x + (float)(L.o[0] - G.o[0]), pq.y + (float)(L.o[1] - G.o[1]),
-                        pq.z + (float)(L.o[2] - G.o[2]), a.fi[it].x);
+        const float4 pq = a.gpos[it];
+        t = make_float4(pq.x, pq.y, pq.z, a.fi[it].x);
       }
       S.tgt[threadIdx.x] = t;  // read after stage_group's opening barrier
     }
@@ -1302,11 +1291,10 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     float px = 0.f, py = 0.f, pz = 0.f;
     float4 fi = make_float4(1.f, 1.f, 0.f, -1.f), vi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (has) {
-      const Leaf &L = a.leaves[a.leaf_of[i]];
-      const float4 q = a.pm[i];
-      px = q.x + (float)(L.o[0] - G.o[0]);
-      py = q.y + (float)(L.o[1] - G.o[1]);
-      pz = q.z + (float)(L.o[2] - G.o[2]);
+      const float4 q = a.gpos[i];
+      px = q.x;
+      py = q.y;
+      pz = q.z;
       fi = a.fi[i];
       vi = a.vu[i];
     }

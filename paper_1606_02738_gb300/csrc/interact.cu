@@ -177,20 +177,17 @@ __global__ void k_ghost(GhostArgs a) {
     const int it = a.niter[i] + 1;
     a.niter[i] = it;
     HIter hs;
-    hs.h = a.h[i];
-    hs.lo = a.hlo[i];
-    hs.hi = a.hhi[i];
-    hs.fprev = a.fprev[i];
+    hs.start(a.h[i], a.hlo[i], a.hhi[i], a.fprev[i]);
     const Leaf &L = a.leaves[a.leaf_of[i]];
     const BoxDev &B = a.boxes[L.box];
     const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
-    const double hcap = fmin(B.L[0], fmin(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
+    const double hcap = B.hcap;
     int st = 0;
     const double h = hs.h;
-    const bool conv = h_newton_step(hs, s.x, s.y, a.n_ngb, a.tol, hcap, &st);
+    const bool conv = h_newton_step(hs, s.x, s.y, a.n_ngb, a.tol * a.n_ngb, hcap, &st);
     if (!conv) {
       a.h[i] = hs.h;
-      a.hf[i] = (float)hs.h;
+      a.hf[i] = hs.hf;
       a.hlo[i] = hs.lo;
       a.hhi[i] = hs.hi;
       a.fprev[i] = hs.fprev;
@@ -200,7 +197,8 @@ __global__ void k_ghost(GhostArgs a) {
     } else {
       float rho, omega, P;
       float4 fi;
-      if (!finalise_density(h, s, (double)a.vu[i].w, a.gamma, &rho, &omega, &P, &fi))
+      if (!finalise_density((float)h, s, a.vu[i].w, (float)(a.gamma - 1.0), &rho, &omega, &P,
+                            &fi))
         st |= kErrNonPhysical;
       a.rho[i] = rho;
       a.omega[i] = omega;

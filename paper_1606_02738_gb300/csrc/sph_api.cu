@@ -55,6 +55,7 @@ struct sph_ctx {
   StoreArrays st{}, st2{};
   float *hf = nullptr;
   float4 *pm = nullptr, *sums = nullptr, *fi = nullptr;
+  float4 *gpos = nullptr;  // position in the particle's batched group frame, mass
   float *skey = nullptr;  // pair-axis sorts: [kAxes][n] keys, rank order per leaf
   int *sidx = nullptr;    // [kAxes][n] leaf-local index of each rank
   int *cnt = nullptr, *niter = nullptr, *nngb = nullptr, *nforce = nullptr, *leaf_of = nullptr;
@@ -209,6 +210,7 @@ FixedLayout fixed_layout(int64_t n, int nb) {
   }
   add(N * sizeof(float));          // hf
   add(N * sizeof(float4));         // pm
+  add(N * sizeof(float4));         // gpos
   add((size_t)kAxes * N * sizeof(float));  // skey
   add((size_t)kAxes * N * sizeof(int));    // sidx
   add(N * sizeof(float4));         // sums
@@ -272,6 +274,7 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   }
   take(c->hf);
   take(c->pm);
+  take(c->gpos);
   take(c->skey);
   take(c->sidx);
   take(c->sums);
@@ -344,8 +347,10 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
         B.n[d] = 3;
         B.w[d] = B.L[d] / 3.0;
         B.iw[d] = 1.0 / B.w[d];
+        B.wf[d] = (float)B.w[d];
       }
       B.eps = (float)(1e-5 * std::max(B.w[0], std::max(B.w[1], B.w[2])));
+      B.hcap = std::min(B.L[0], std::min(B.L[1], B.L[2])) / (3.0 * (1.0 + 1e-6));
       B.cell_base = base;
       base += 27;
       continue;
@@ -374,9 +379,11 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
     for (int d = 0; d < 3; ++d) {
       B.w[d] = B.L[d] / B.n[d];
       B.iw[d] = 1.0 / B.w[d];
+      B.wf[d] = (float)B.w[d];
       wmax = std::max(wmax, B.w[d]);
     }
     B.eps = (float)(1e-5 * wmax);
+    B.hcap = lmin / (3.0 * (1.0 + 1e-6));
     B.cell_base = base;
     base += B.n[0] * B.n[1] * B.n[2];
   }
@@ -612,6 +619,7 @@ GroupBuildArgs group_args(sph_ctx *c) {
   ga.leaf_of = c->leaf_of;
   ga.pm = c->pm;
   ga.hf = c->hf;
+  ga.gpos = c->gpos;
   return ga;
 }
 
@@ -712,6 +720,7 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   da.ctr = c->ctr;
   da.queue = as<int>(c->gqueue);  // ctr->queued, queued2 were zeroed with the counters
   da.queue2 = as<int>(c->gqueue) + c->n_groups;
+  da.gpos = c->gpos;
   da.nodes = as<Node>(c->nodes);
   tic(c, kDens);
   launch_density_batched(da, c->stream);
@@ -871,6 +880,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   fa.ctr = c->ctr;
   fa.queue = as<int>(c->gqueue);
   fa.queue2 = as<int>(c->gqueue) + c->n_groups;
+  fa.gpos = c->gpos;
   fa.nodes = as<Node>(c->nodes);
   fa.boxes = c->boxes_d;
   tic(c, kForce);

@@ -43,6 +43,9 @@ struct BoxDev {
   float eps;       // pruning margin in top-cell-relative units
   float pad;
   double iw[3];    // 1 / w
+  double hcap;     // largest allowed h: min(L) / (3 (1 + 1e-6))
+  float wf[3];     // w rounded to FP32 (neighbour-cell shifts in the walks)
+  float pad2;
 };
 
 struct Node {
@@ -121,44 +124,112 @@ __device__ __forceinline__ float dw_only(float q) {
 struct HIter {
   double h;      // current smoothing length
   double lo, hi; // bracket: N(lo) < n_ngb <= N(hi); hi = 1e308 while open
+  float hf;      // h rounded to FP32 (the kernels' working copy)
   float fprev;   // |N - n_ngb| of the previous pass
+  __device__ __forceinline__ void start(double h0, double lo0, double hi0, float fprev0) {
+    h = h0;
+    lo = lo0;
+    hi = hi0;
+    hf = (float)h0;
+    fprev = fprev0;
+  }
 };
 
 // Weighted neighbour number N = (32/3) sum w and dN/dh = -(32/(3h)) sum q w'
-// from the FP32 sums `s` at h. Returns true when h is accepted: |N - n_ngb| <=
-// tol n_ngb, or the next step would move h by at most 5e-7 h (the resolution
-// of FP32 sums). Otherwise moves h by Newton on ln N(ln h) (exponent
-// s = h N'/N = -(sum q w') / (sum w) measured, so steep N near clusters does
-// not overshoot), clamped to [h/8, 2h] and to hcap (L/3), bisecting the
-// bracket when the step leaves it or |f| failed to halve well above the FP32
-// noise. *st receives kErrBoxTooSmall when the root lies beyond hcap.
-// The bracket and h are FP64; the step factor is FP32 (a proposal that the
-// next pass corrects; FP64 exp/log/division are slow on this part).
+// from the FP32 sums at h. Returns true when h is accepted: |N - n_ngb| <=
+// tol_n (= h_tol n_ngb; this test is FP64), or the next step would move h by
+// at most 5e-7 h (the resolution of FP32 sums). Otherwise moves h by Newton
+// on ln N(ln h) (exponent s = h N'/N = -(sum q w') / (sum w) measured, so
+// steep N near clusters does not overshoot), clamped to [h/8, 2h] and to
+// hcap (L/3), bisecting the bracket when the step leaves it or |f| failed to
+// halve well above the FP32 noise. *st receives kErrBoxTooSmall when the
+// root lies beyond hcap. The bracket and h are FP64; the step factor, the
+// halving test and the Newton step-size test are FP32 (FP64 runs at 1/64 of
+// the FP32 rate on this part, so the pass does as few FP64 operations as
+// the FP64 test and bracket need).
 __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, double n_ngb,
-                                              double tol, double hcap, int *st) {
+                                              double tol_n, double hcap, int *st) {
+  const double f = fma(32.0 / 3.0, (double)sw, -n_ngb);
+  if (fabs(f) <= tol_n) return true;
   const double h = it.h;
-  const double N = (32.0 / 3.0) * (double)sw;
-  const double f = N - n_ngb;
-  if (fabs(f) <= tol * n_ngb) return true;
+  const float ff = (float)f;
   double lo = it.lo, hi = it.hi;
   if (f < 0.0)
     lo = h;
   else
     hi = h;
+  const bool open = hi >= 1e300;
   const float s_ln = sw > 0.f ? -sqdw / sw : 0.f;  // d ln N / d ln h
   float fac = 2.f;
   if (s_ln > 0.f) fac = __expf(__logf((float)n_ngb / ((32.f / 3.f) * sw)) / s_ln);
   fac = fminf(fmaxf(fac, 0.125f), 2.f);
   double hn = h * (double)fac;
-  if (hi < 1e300 && (!(hn > lo && hn < hi) ||
-                     (fabs(f) > 0.5 * (double)it.fprev && fabs(f) > 1e-4 * n_ngb)))
+  bool newton = true;
+  if (!open && (!(hn > lo && hn < hi) ||
+                (fabsf(ff) > 0.5f * it.fprev && fabsf(ff) > 1e-4f * (float)n_ngb))) {
     hn = 0.5 * (lo + hi);
-  it.fprev = (float)fabs(f);
+    newton = false;
+  }
+  it.fprev = fabsf(ff);
   if (hn > hcap) {
     if (h >= hcap * (1.0 - 1e-12) && f < 0.0) *st |= kErrBoxTooSmall;
     hn = hcap;
+    newton = false;
   }
-  if (fabs(hn - h) <= 5e-7 * h && !(*st & kErrBoxTooSmall)) return true;
+  const bool tiny = newton ? fabsf(fac - 1.f) <= 5e-7f : fabs(hn - h) <= 5e-7 * h;
+  if (tiny && !(*st & kErrBoxTooSmall)) return true;
+  it.h = hn;
+  it.hf = (float)hn;
+  it.lo = lo;
+  it.hi = hi;
+  return false;
+}
+
+// The same step with h and its bracket held in FP32 (the batched kernels:
+// h needs ~3e-6 relative accuracy for rho to 1e-5, FP32 gives 6e-8); the
+// acceptance test |N - n_ngb| <= tol_n stays FP64. hi = +inf while open.
+struct HIterF {
+  float h, lo, hi, fprev;
+  __device__ __forceinline__ void start(float h0) {
+    h = h0;
+    lo = 0.f;
+    hi = __int_as_float(0x7f800000);
+    fprev = __int_as_float(0x7f800000);
+  }
+};
+
+__device__ __forceinline__ bool h_newton_step_f(HIterF &it, float sw, float sqdw, double n_ngb,
+                                                double tol_n, float hcap, int *st) {
+  const double f = fma(32.0 / 3.0, (double)sw, -n_ngb);
+  if (fabs(f) <= tol_n) return true;
+  const float ff = (float)f;  // |f| > tol_n: no underflow, the sign survives
+  const float h = it.h;
+  float lo = it.lo, hi = it.hi;
+  if (ff < 0.f)
+    lo = h;
+  else
+    hi = h;
+  const bool open = !(hi < 3e38f);
+  const float nn = (float)n_ngb;
+  const float s_ln = sw > 0.f ? -sqdw / sw : 0.f;  // d ln N / d ln h
+  float fac = 2.f;
+  if (s_ln > 0.f) fac = __expf(__logf(nn / ((32.f / 3.f) * sw)) / s_ln);
+  fac = fminf(fmaxf(fac, 0.125f), 2.f);
+  float hn = h * fac;
+  bool newton = true;
+  if (!open && (!(hn > lo && hn < hi) ||
+                (fabsf(ff) > 0.5f * it.fprev && fabsf(ff) > 1e-4f * nn))) {
+    hn = 0.5f * (lo + hi);
+    newton = false;
+  }
+  it.fprev = fabsf(ff);
+  if (hn > hcap) {
+    if (h >= hcap && ff < 0.f) *st |= kErrBoxTooSmall;
+    hn = hcap;
+    newton = false;
+  }
+  const bool tiny = newton ? fabsf(fac - 1.f) <= 5e-7f : fabsf(hn - h) <= 5e-7f * h;
+  if (tiny && !(*st & kErrBoxTooSmall)) return true;
   it.h = hn;
   it.lo = lo;
   it.hi = hi;
@@ -170,23 +241,22 @@ __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, d
 // rho (Eq. rho), Omega = 1 + h/(3 rho) drho/dh, P = (gamma - 1) rho u, and the
 // force-stage record (h, 1/h, A (8/pi) h^-4, h^2) with A = P / (Omega rho^2).
 // FP32 arithmetic (relative error ~1e-7).
-__device__ __forceinline__ bool finalise_density(double h, float4 s, double u, double gamma,
+__device__ __forceinline__ bool finalise_density(float hf, float4 s, float u, float gm1,
                                                  float *rho_o, float *omega_o, float *P_o,
                                                  float4 *fi_o) {
   const float c8pi = 2.546479089470325f;  // 8 / pi
-  const float hf = (float)h;
   const float hinv = 1.f / hf;
   const float hinv3 = hinv * hinv * hinv;
   const float rho = c8pi * s.z * hinv3;
   const float drho = -c8pi * s.w * hinv3 * hinv;
   const float omega = 1.f + hf / (3.f * rho) * drho;
-  const float P = (float)(gamma - 1.0) * rho * (float)u;
+  const float P = gm1 * rho * u;
   const float A = P / (omega * rho * rho);
   *rho_o = rho;
   *omega_o = omega;
   *P_o = P;
   *fi_o = make_float4(hf, hinv, A * c8pi * hinv3 * hinv, hf * hf);
-  return rho > 0.f && omega > 0.f && u >= 0.0;
+  return rho > 0.f && omega > 0.f && u >= 0.f;
 }
 
 // ---- pair-axis sorts (Section 3.1: particles are sorted along the axis of
@@ -455,6 +525,7 @@ struct GroupBuildArgs {
   const int *leaf_of;
   const float4 *pm;
   const float *hf;
+  float4 *gpos;          // out (geometry): position in the group frame, mass
 };
 void launch_group_count(const GroupBuildArgs &a, cudaStream_t s);
 void launch_group_fill(const GroupBuildArgs &a, cudaStream_t s);
@@ -490,6 +561,7 @@ struct BatchDensArgs {
   const Leaf *leaves;
   const int *leaf_of;
   const float4 *pm;
+  const float4 *gpos;    // targets: position in their group's frame, mass
   const BoxDev *boxes;
   double *h;
   float *hf;
@@ -519,6 +591,7 @@ struct BatchForceArgs {
   const Leaf *leaves;
   const int *leaf_of;
   const float4 *pm;
+  const float4 *gpos;    // targets: position in their group's frame, mass
   const float4 *fi;
   const float4 *vu;
   float4 *acc;
