@@ -120,6 +120,14 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def whole_job_rate(d: Dist, units: float, ms: float) -> tuple[float, float]:
+    """Units all ranks processed / the slowest rank's time (units/s), and that
+    time in ms (0 units or 0 ms -> rate 0)."""
+    ms_max = d.reduce(float(ms), "MAX")
+    total = d.reduce(float(units), "SUM")
+    return (total / (ms_max / 1000.0) if ms_max > 0 else 0.0), ms_max
+
+
 # ---------------------------------------------------------------- clocks
 
 class Clocks:
@@ -327,9 +335,7 @@ def run_ours(args, d: Dist):
     inter_d = s1["total_density_interactions"] - s0["total_density_interactions"]
     inter_f = s1["total_force_interactions"] - s0["total_force_interactions"]
     inter = inter_d + inter_f
-    ms_max = d.reduce(ms, "MAX")
-    inter_all = d.reduce(float(inter), "SUM")
-    value = inter_all / (ms_max / 1000.0)
+    value, ms_max = whole_job_rate(d, inter, ms)
 
     # roofline of the interaction kernels (CUDA events around each launch,
     # recorded by the library on this stream)
@@ -399,9 +405,8 @@ def run_ours(args, d: Dist):
         e2e_ms += a.elapsed_time(b)
         e2e_inter += (sb["total_density_interactions"] - sa["total_density_interactions"] +
                       sb["total_force_interactions"] - sa["total_force_interactions"])
-    e2e_ms_max = d.reduce(e2e_ms, "MAX")
-    e2e_val = (d.reduce(float(e2e_inter), "SUM") / (e2e_ms_max / 1000.0)
-               if e2e_ms_max > 0 else None)
+    e2e_val, e2e_ms_max = whole_job_rate(d, e2e_inter, e2e_ms)
+    e2e_val = e2e_val if e2e_ms_max > 0 else None
 
     # the other interaction form, same workload, same protocol (comparison)
     other = None
@@ -448,6 +453,9 @@ def run_ours(args, d: Dist):
                        "mode": args.mode, "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": "replicas" if d.world > 1 else "single GPU",
                        "interactions_per_step": inter / args.steps,
+                       "particle_updates_per_s": p.n * d.world / (ms_max / args.steps / 1000.0),
+                       "pairs_tested_last_step": s1["density_pair_candidates"] +
+                       s1["force_pair_candidates"],
                        "density_passes_last_step": s1["density_passes"],
                        "batched_fallbacks_last_step": s1["batched_fallbacks"],
                        "fallback_causes_last_step": s1["fallback_causes"],

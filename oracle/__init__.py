@@ -17,9 +17,12 @@ decomposition for strong scaling on more than 100,000 cores", PASC '16.
   Section 2, Eqs. (dvdt), (dudt)  accelerations, du/dt    -> force()
   Section 3.1, integrator task    kick/drift update       -> kdk_step()
 
-Readings where the paper is silent (cubic-spline kernel with support h,
-weighted neighbour target 48, kick-drift-kick with a global dt, predicted v and
-u at the force evaluation) are listed in the design doc.
+Where the paper is silent this oracle reads it as follows: the smoothing
+kernel is the cubic spline with support h; h solves (32/3) sum_j w(r_ij/h) =
+n_ngb (48 by default), the weighted neighbour number, which is monotone in h
+so the root is unique; the sums include j = i; the integrator is
+kick-drift-kick with one global dt, and the mid-step force uses v and u
+predicted to the end of the step.
 """
 from __future__ import annotations
 
