@@ -407,20 +407,21 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
 constexpr int kNW = 4;           // warps per block, one group per block
 constexpr int kSub = 8;          // targets per warp
 constexpr int kSlice = 4;        // lanes per target
-constexpr int kStageD = 1280;    // density stage entries per group
-constexpr int kStageF = 1024;    // force stage entries per group
+constexpr int kStageD = 1152;    // density stage entries per group (6 blocks per SM)
+constexpr int kStageF = 704;     // force stage entries per group (7 blocks per SM)
 constexpr int kBigStageD = 4096; // second tier: groups whose stage overflowed the first
 constexpr int kBigStageF = 3072;
-constexpr int kCandD = 1280;     // density entries kept per warp
-constexpr int kCandF = 640;      // force entries kept per warp
-constexpr int kLane = 32;        // list entries per lane
+constexpr int kCandD = 1152;     // density entries kept per warp
+constexpr int kCandF = 512;      // force entries kept per warp
+constexpr int kLaneD = 32;       // density list entries per lane
+constexpr int kLaneF = 28;       // force list entries per lane
 
 template <int NS>
 struct DensSmem {
   float4 tgt[32];                           // tight stage: target position (group frame), radius
   float4 stage[NS];                         // position in the group frame, m
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
-  unsigned short list[kNW][kLane * 32];     // [entry][lane]
+  unsigned short list[kNW][kLaneD * 32];     // [entry][lane]
   int wcount[kNW];
 };
 
@@ -431,7 +432,7 @@ struct ForceSmem {
   float2 sf[NS];                            // A (8/pi) h^-4, h^2
   int sj[NS];                               // particle index (velocity read on use)
   unsigned short cand[kNW][kCandF];
-  unsigned short list[kNW][kLane * 32];
+  unsigned short list[kNW][kLaneF * 32];
   int wcount[kNW];
 };
 
@@ -688,7 +689,7 @@ struct DensAcc {
 };
 
 template <bool KAHAN, int NS>
-__global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
+__global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 6 : 1)
     k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
     sub_box(has, px, py, pz, blo, bhi);
 
     bool failed = false, fin = !has, need_list = has, need_filter = true;
-    // 0: per-lane lists; 1: a lane's list outgrew kLane, the warp reads its
+    // 0: per-lane lists; 1: a lane's list outgrew kLaneD, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandD, the warp reads
     // the whole stage (slower, same sums)
     int mode = 0;
@@ -785,12 +786,12 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 5 : 1)
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (r2 < rl2) {
-            if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
+            if (cnt < kLaneD) list[cnt * 32 + lane] = (unsigned short)k;
             ++cnt;
           }
         }
         need_list = false;
-        if (__any_sync(0xffffffffu, cnt > kLane)) mode = 1;
+        if (__any_sync(0xffffffffu, cnt > kLaneD)) mode = 1;
         __syncwarp();
       }
       // partial sums over this lane's slice at the current h
@@ -1245,7 +1246,7 @@ struct ForceAcc {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
+__global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
     k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
@@ -1304,7 +1305,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
     const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, kCandF, lane);
-    // 0: per-lane lists; 1: a list outgrew kLane, the warp reads its
+    // 0: per-lane lists; 1: a list outgrew kLaneF, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandF, it reads the
     // whole stage (ncand is warp-uniform)
     int mode = ncand > kCandF ? 2 : 0;
@@ -1319,12 +1320,12 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 5 : 1)
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-          if (cnt < kLane) list[cnt * 32 + lane] = (unsigned short)k;
+          if (cnt < kLaneF) list[cnt * 32 + lane] = (unsigned short)k;
           ++cnt;
         }
       }
       if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
-      if (__any_sync(0xffffffffu, cnt > kLane)) mode = 1;
+      if (__any_sync(0xffffffffu, cnt > kLaneF)) mode = 1;
       __syncwarp();
     }
     ForceAcc acc;

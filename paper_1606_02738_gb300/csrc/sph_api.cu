@@ -750,6 +750,13 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
       ++c->last_rebuilds;
       TRY(density_batched(c, vu_for_P));
     }
+    if (c->ctr_h->fallback == 0 && !(c->ctr_h->status & kErrHGrid)) {
+      // every particle finished in the batched kernels: no per-pass remainder
+      c->total_dens_inter += c->ctr_h->dens_inter;
+      c->density_valid = true;
+      c->force_valid = false;
+      return SPH_OK;
+    }
   }
   const int max_passes = c->p.max_iter + 8;
   for (int pass = 0;; ++pass) {
