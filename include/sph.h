@@ -92,7 +92,12 @@ typedef struct {
                       per-pass kernels visit only the source particles whose key along a
                       pair's axis is within reach; 0: visit whole source leaves (same
                       results, more pairs tested). The batched kernels do not use them. */
-  int reserved[2]; /* zero */
+  int reuse_grid;  /* 1: sph_step keeps the grid of the last regrid while every particle
+                      stays within reach of its top cell (h_max + 2 x the largest distance
+                      outside its cell <= the cell width), refreshing positions and boxes
+                      only, and runs those steps as one CUDA graph in the batched FP32
+                      form; 0: regrid every step (same results up to summation order) */
+  int reserved[1]; /* zero */
 } sph_params;
 
 typedef struct {
@@ -149,10 +154,13 @@ typedef struct {
   int32_t tier2_groups[2];
   int32_t tier3_entries[2];
   int64_t sort_launches;      /* pair-axis sort launches (cumulative since sph_create) */
+  int64_t reused_steps;       /* steps run on the previous step's grid (cumulative) */
+  int64_t redone_steps;       /* of those, steps redone on a new grid because a particle had
+                                 moved too far from its top cell (cumulative) */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,
- * n_split = 64, FP32, batched mode, pair sorts on, profiling off. */
+ * n_split = 64, FP32, batched mode, pair sorts on, grid reuse on, profiling off. */
 void sph_default_params(sph_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a

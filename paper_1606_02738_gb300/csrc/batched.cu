@@ -169,7 +169,7 @@ __global__ void k_group_geometry(GroupBuildArgs a) {
   const Leaf &L0 = a.leaves[a.leaf_of[start]];
   const double o[3] = {L0.o[0], L0.o[1], L0.o[2]};
   float flo[3] = {3e38f, 3e38f, 3e38f}, fhi[3] = {-3e38f, -3e38f, -3e38f};
-  float tlo[3] = {3e38f, 3e38f, 3e38f}, thi[3] = {0.f, 0.f, 0.f};
+  float tlo[3] = {3e38f, 3e38f, 3e38f}, thi[3] = {-3e38f, -3e38f, -3e38f};
   if (lane < count) {
     const int i = start + lane;
     const Leaf &L = a.leaves[a.leaf_of[i]];
@@ -178,7 +178,7 @@ __global__ void k_group_geometry(GroupBuildArgs a) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const float f = pq[d] + (float)(L.o[d] - o[d]);
-      const float t = fmaxf((float)(L.o[d] + (double)pq[d]), 0.f);
+      const float t = (float)(L.o[d] + (double)pq[d]);
       flo[d] = fhi[d] = f;
       tlo[d] = thi[d] = t;
     }

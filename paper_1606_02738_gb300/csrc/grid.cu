@@ -233,8 +233,8 @@ void launch_cell_scatter(const GridArgs &g, cudaStream_t s) {
 
 __device__ __forceinline__ void reset_bounds(Node &nd) {
   for (int d = 0; d < 3; ++d) {
-    nd.lo[d] = __int_as_float(0x7f800000);
-    nd.hi[d] = 0.f;
+    nd.lo[d] = __int_as_float(0x7f800000);   // +inf
+    nd.hi[d] = __int_as_float(0xff800000);   // -inf
   }
   nd.hmax = 0.f;
 }
@@ -414,15 +414,30 @@ void launch_sort_leaves(const Leaf *leaves, int n_leaves, int *order, const int 
 
 // --------------------------------------------------- leaf geometry / hmax
 
-__device__ __forceinline__ void atomic_min_pos(float *a, float v) {
-  atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
-}
-__device__ __forceinline__ void atomic_max_pos(float *a, float v) {
+__device__ __forceinline__ void atomic_max_pos(float *a, float v) {  // a, v >= 0
   atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+}
+// Float min / max of any sign by integer atomics: non-negative floats order
+// like their bits as signed ints, negative ones inversely as unsigned ints.
+__device__ __forceinline__ void atomic_min_f(float *a, float v) {
+  if (v >= 0.f)
+    atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
+  else
+    atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float *a, float v) {
+  if (v >= 0.f)
+    atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+  else
+    atomicMin(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
 }
 
 // One warp per leaf: leaf-relative FP32 positions (cell-relative precision)
-// and the leaf bounding box (top-cell-relative, >= 0), pushed up the tree.
+// and the leaf bounding box (top-cell-relative), pushed up the tree. Each
+// position is taken at the periodic image nearest its top cell, so after a
+// drift without a regrid a particle that crossed the box boundary stays
+// beside its cell; *a.maxout (if given) receives the largest distance by
+// which a particle lies outside its top cell (float bits).
 __global__ void k_leaf_geometry(GeomArgs a) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -432,18 +447,24 @@ __global__ void k_leaf_geometry(GeomArgs a) {
   const Node &nd = a.nodes[L.node];
   int c[3];
   cell_coords(B, nd.cell - B.cell_base, c);
-  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {0.f, 0.f, 0.f};
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  float out = 0.f;
   for (int k = lane; k < L.count; k += 32) {
     const int s = L.start + k;
     const double x[3] = {a.x0[s], a.x1[s], a.x2[s]};
     float p[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double rel = x[d] - (double)c[d] * B.w[d];
+      double rel = x[d] - (double)c[d] * B.w[d];
+      if (rel > 0.5 * B.L[d])
+        rel -= B.L[d];
+      else if (rel < -0.5 * B.L[d])
+        rel += B.L[d];
       p[d] = (float)(rel - L.o[d]);
-      const float rf = fmaxf((float)rel, 0.f);
+      const float rf = (float)rel;
       lo[d] = fminf(lo[d], rf);
       hi[d] = fmaxf(hi[d], rf);
+      out = fmaxf(out, fmaxf(-rf, rf - B.wf[d]));
     }
     a.pm[s] = make_float4(p[0], p[1], p[2], a.m[s]);
   }
@@ -454,17 +475,39 @@ __global__ void k_leaf_geometry(GeomArgs a) {
       hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
     }
   }
+  for (int o = 16; o; o >>= 1) out = fmaxf(out, __shfl_xor_sync(0xffffffffu, out, o));
   if (lane == 0) {
     int id = L.node;
     while (id >= 0) {
       Node *n = &a.nodes[id];
       for (int d = 0; d < 3; ++d) {
-        atomic_min_pos(&n->lo[d], lo[d]);
-        atomic_max_pos(&n->hi[d], hi[d]);
+        atomic_min_f(&n->lo[d], lo[d]);
+        atomic_max_f(&n->hi[d], hi[d]);
       }
       id = n->parent;
     }
+    if (a.maxout && out > 0.f) atomicMax(&a.maxout[L.box], __float_as_uint(out));
   }
+}
+
+// Empty bounding boxes for every node (before k_leaf_geometry refills them).
+__global__ void k_reset_boxes(Node *nodes, int n_nodes) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n_nodes) return;
+  for (int d = 0; d < 3; ++d) {
+    nodes[id].lo[d] = __int_as_float(0x7f800000);
+    nodes[id].hi[d] = __int_as_float(0xff800000);
+  }
+}
+
+void launch_refresh_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s) {
+  if (n_nodes > 0) {
+    k_reset_boxes<<<(n_nodes + 255) / 256, 256, 0, s>>>(a.nodes, n_nodes);
+    note_launch();
+  }
+  if (a.n_leaves <= 0) return;
+  k_leaf_geometry<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a);
+  note_launch();
 }
 
 __global__ void k_reset_hmax(Node *nodes, int n_nodes) {
@@ -498,6 +541,39 @@ void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s) {
   k_reset_hmax<<<(n_nodes + 255) / 256, 256, 0, s>>>(a.nodes, n_nodes); note_launch();
   if (a.n_leaves <= 0) return;
   k_leaf_hmax<<<(a.n_leaves * 32 + 255) / 256, 256, 0, s>>>(a); note_launch();
+}
+
+// Is the grid still valid for the h just computed? A pair in range is
+// found among the 27 top cells around the target's cell as long as
+// h_max (1 + 1e-6) + 2 out <= w for every box, with `out` the largest
+// distance by which a particle lies outside its top cell (k_leaf_geometry);
+// otherwise kErrHGrid asks for a regrid. hext[b] holds box b's largest h
+// (k_h_extremes bit patterns).
+__global__ void k_grid_check(const BoxDev *boxes, int nb, const unsigned long long *hext,
+                             const unsigned *boxout, int *status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const BoxDev &B = boxes[b];
+  const double hmax = __longlong_as_double((long long)hext[b]);
+  const double out = (double)__uint_as_float(boxout[b]);
+  const double wmin = fmin(B.w[0], fmin(B.w[1], B.w[2]));
+  if (B.count > 0 && hmax * (1.0 + 1e-6) + 2.0 * out > wmin) atomicOr(status, kErrHGrid);
+}
+
+// hext = {0 for every box, ~0 (minimum), 0 (maximum)} on the device.
+__global__ void k_hext_init(unsigned long long *hext, int nb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nb + 2) hext[k] = k == nb ? ~0ull : 0ull;
+}
+
+void launch_grid_check(const double *h, int n, const BoxDev *boxes, int nb,
+                       unsigned long long *hext, const unsigned *boxout, int *status,
+                       cudaStream_t s) {
+  k_hext_init<<<(nb + 2 + 255) / 256, 256, 0, s>>>(hext, nb);
+  note_launch();
+  launch_h_extremes(h, n, boxes, nb, hext, hext + nb, s);
+  k_grid_check<<<(nb + 255) / 256, 256, 0, s>>>(boxes, nb, hext, boxout, status);
+  note_launch();
 }
 
 // Starting guess for the h iteration from the number density of each octree

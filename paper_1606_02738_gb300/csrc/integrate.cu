@@ -126,7 +126,7 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
   const float4 p = make_float4(fmaf(a.x, hdt, v.x), fmaf(a.y, hdt, v.y), fmaf(a.z, hdt, v.z),
                                fmaf(a.w, hdt, v.w));
   st.vu_pred[s] = p;
-  if (!(p.w > 0.f) || !(v.w > 0.f)) atomicOr(&ctr->status, kErrNonPhysical);
+  if (!(p.w > 0.f) || !(v.w > 0.f)) atomicOr(&ctr->step_status, kErrNonPhysical);
 }
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
@@ -147,7 +147,7 @@ __global__ void k_kick(StoreArrays st, int n, double dt, DevCounters *ctr) {
   v.w = fmaf(a.w, hdt, v.w);
   st.vu[s] = v;
   st.vu_pred[s] = v;
-  if (!(v.w > 0.f)) atomicOr(&ctr->status, kErrNonPhysical);
+  if (!(v.w > 0.f)) atomicOr(&ctr->step_status, kErrNonPhysical);
 }
 
 void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s) {

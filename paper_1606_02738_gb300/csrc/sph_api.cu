@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -83,9 +84,14 @@ struct sph_ctx {
 
   bool loaded = false, grid_valid = false, density_valid = false, force_valid = false;
   bool sorts_valid = false;  // pair-axis sorts match the current grid
+  bool groups_geom_valid = false;  // group frames and boxes match the current positions
+  bool grid_reusable = false;      // the last step's grid passed the reach check
+  int regrids_in_step = 0;
+  unsigned *boxout = nullptr;      // per box: largest distance outside the top cell
   int last_passes = 0, last_rebuilds = 0;
   // cumulative counters and stage timers
   long long launches = 0, dens_launches = 0, force_launches = 0, sort_launches = 0;
+  long long reused_steps = 0, redone_steps = 0;
   unsigned long long total_dens_inter = 0, total_force_inter = 0;
   bool force_pending = false;  // force counters on the device not yet added to the totals
   cudaEvent_t ev[7][2] = {};
@@ -228,6 +234,7 @@ FixedLayout fixed_layout(int64_t n, int nb) {
   for (int k = 0; k < 3; ++k) add(N * sizeof(unsigned));  // mkey msrt mscr
   add(3 * N * sizeof(double));     // wx
   add((size_t)(nb + 2) * sizeof(unsigned long long));     // hext
+  add((size_t)nb * sizeof(unsigned));                      // boxout
   add((size_t)nb * sizeof(BoxDev));                        // boxes
   return L;
 }
@@ -301,6 +308,7 @@ int alloc_fixed(sph_ctx *c, int64_t n, int nb) {
   take(c->mscr);
   take(c->wx);
   take(c->hext);
+  take(c->boxout);
   take(c->boxes_d);
   c->alloc_n = n;
   c->alloc_nb = nb;
@@ -516,10 +524,13 @@ int build_grid_inner(sph_ctx *c, bool from_caller, const float *cv, const float 
               c->st.x0, c->st.x1, c->st.x2, c->st.m, c->hf, c->pm};
   launch_leaf_geometry(ga, n_nodes, c->stream);
   TRY(sync_check(c));
+  CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
   c->grid_valid = true;
   c->groups_valid = false;
+  c->groups_geom_valid = false;
   c->density_valid = false;
   c->force_valid = false;
+  ++c->regrids_in_step;
   return SPH_OK;
 }
 
@@ -642,6 +653,7 @@ int build_groups(sph_ctx *c) {
   launch_group_fill(ga, c->stream);
   launch_group_geometry(ga, c->stream);
   c->groups_valid = true;
+  c->groups_geom_valid = true;
   return sync_check(c);
 }
 
@@ -685,6 +697,10 @@ constexpr float kSkinList = 1.05f;   // per-lane list radius = 1.05 x the lane's
 // per-pass loop.
 int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   if (!c->groups_valid) TRY(build_groups(c));
+  if (!c->groups_geom_valid) {  // positions moved on an unchanged grid
+    launch_group_geometry(group_args(c), c->stream);
+    c->groups_geom_valid = true;
+  }
   GroupBuildArgs ga = group_args(c);
   launch_group_hmax(ga, c->stream);
   GeomArgs gg = geom_args(c);
@@ -737,7 +753,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   const int n = c->n;
   launch_h_guess(geom_args(c), c->p.n_ngb, c->st.h, c->hf, c->stream);
   launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
-  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
   c->last_passes = 0;
   c->last_rebuilds = 0;
   if (c->p.mode == SPH_MODE_BATCHED) {
@@ -746,7 +762,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
       // some h outgrew its top cell: regrid with the grown h and start again
       TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
       launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, n, c->stream);
-      CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
+      CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
       ++c->last_rebuilds;
       TRY(density_batched(c, vu_for_P));
     }
@@ -961,6 +977,62 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   return SPH_OK;
 }
 
+// After a drift on an unchanged grid: leaf-relative positions, node boxes
+// and the per-box out-of-cell distance from the new x (A1 and A2 skipped).
+int refresh_grid(sph_ctx *c) {
+  tic(c, kGrid);
+  CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
+  GeomArgs ga = geom_args(c);
+  ga.maxout = c->boxout;
+  launch_refresh_geometry(ga, c->n_nodes, c->stream);
+  toc(c, kGrid);
+  c->groups_geom_valid = false;
+  c->sorts_valid = false;
+  c->density_valid = false;
+  c->force_valid = false;
+  return sync_check(c);
+}
+
+// The state a step starts from (positions, h, v and u, accelerations), kept
+// in the second store copy so a step on a reused grid can be redone.
+void copy_step_state(sph_ctx *c, const StoreArrays &from, const StoreArrays &to) {
+  const size_t n = (size_t)c->n;
+  cudaMemcpyAsync(to.x0, from.x0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(to.x1, from.x1, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(to.x2, from.x2, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(to.h, from.h, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(to.vu, from.vu, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(to.acc, from.acc, n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream);
+}
+
+// One kick-drift-kick step (Section 3.1 integrator task around the density,
+// ghost and force tasks), on the grid of the last regrid when `reuse`.
+// Leaves the status words in ctr_h (read once at the end).
+int step_once(sph_ctx *c, double dt, bool reuse) {
+  c->regrids_in_step = 0;
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
+  if (reuse) copy_step_state(c, c->st, c->st2);
+  tic(c, kInteg);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+  toc(c, kInteg);
+  c->density_valid = false;
+  c->force_valid = false;
+  if (reuse) {
+    TRY(refresh_grid(c));
+  } else {
+    c->grid_valid = false;
+    TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+  }
+  TRY(density_impl(c, c->st.vu_pred));
+  TRY(force_impl(c, c->st.vu_pred));
+  tic(c, kInteg);
+  launch_kick(c->st, c->n, dt, c->ctr, c->stream);
+  toc(c, kInteg);
+  launch_grid_check(c->st.h, c->n, c->boxes_d, c->nb, c->hext, c->boxout, &c->ctr->step_status,
+                    c->stream);
+  return read_counters(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -976,6 +1048,7 @@ void sph_default_params(sph_params *p) {
   p->precision = SPH_PREC_FP32;
   p->mode = SPH_MODE_BATCHED;
   p->pair_sort = 1;
+  p->reuse_grid = 1;
 }
 
 int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
@@ -988,7 +1061,7 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       q.n_split < 8 || q.n_split > 256 ||
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
-      (q.pair_sort != 0 && q.pair_sort != 1))
+      (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1))
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;
@@ -1057,10 +1130,11 @@ int sph_init(sph_ctx *c, int n_boxes, const int64_t *box_offsets, const double *
     B.count = (int)(box_offsets[b + 1] - box_offsets[b]);
   }
   c->loaded = false;
+  c->grid_reusable = false;
   TRY(alloc_fixed(c, n, n_boxes));
   CUDA_TRY(cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * n_boxes,
                            cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->status, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   launch_validate(x, v, m, u, h, c->n, &c->ctr->status, c->stream);
   TRY(read_counters(c));
   if (c->ctr_h->status & kErrInvalidInput)
@@ -1099,21 +1173,21 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
   if (!(dt > 0.0) || !std::isfinite(dt) || n_steps < 0)
     return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
   for (int s = 0; s < n_steps; ++s) {
-    CUDA_TRY(cudaMemsetAsync(&c->ctr->status, 0, sizeof(int), c->stream));
-    tic(c, kInteg);
-    launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
-    toc(c, kInteg);
-    c->grid_valid = false;
-    c->density_valid = false;
-    c->force_valid = false;
-    TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
-    TRY(density_impl(c, c->st.vu_pred));
-    TRY(force_impl(c, c->st.vu_pred));
-    tic(c, kInteg);
-    launch_kick(c->st, c->n, dt, c->ctr, c->stream);
-    toc(c, kInteg);
-    TRY(read_counters(c));
-    TRY(check_status(c, c->ctr_h->status));
+    const bool reuse = c->p.reuse_grid && c->grid_reusable && c->grid_valid;
+    TRY(step_once(c, dt, reuse));
+    if (reuse) ++c->reused_steps;
+    int st = c->ctr_h->step_status;
+    if ((st & kErrHGrid) && reuse && c->regrids_in_step == 0) {
+      ++c->redone_steps;
+      // a particle moved too far from its top cell for the h it now has:
+      // back to the step's starting state and redo the step on a new grid
+      copy_step_state(c, c->st2, c->st);
+      launch_h_to_float(c->st.h, c->hf, c->n, c->stream);
+      TRY(step_once(c, dt, false));
+      st = c->ctr_h->step_status;
+    }
+    TRY(check_status(c, (c->ctr_h->status | st) & ~kErrHGrid));
+    c->grid_reusable = !(st & kErrHGrid);
   }
   return sync_check(c);
 }
@@ -1192,6 +1266,8 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
     out->tier3_entries[k] = c->ctr_h->queued2[k];
   }
   out->sort_launches = c->sort_launches;
+  out->reused_steps = c->reused_steps;
+  out->redone_steps = c->redone_steps;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
   double hmin = 0, hmax = 0;

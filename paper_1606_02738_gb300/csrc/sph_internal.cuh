@@ -96,6 +96,8 @@ struct DevCounters {
   int why[4];                         // batched fallbacks: density third-tier walk (frontier
                                       // or h beyond the top cell), density passes, force
                                       // third-tier walk, (zero)
+  int step_status;                    // kErr* bits of the kicks and the grid check (last
+                                      // field: the density's counter reset keeps it)
 };
 
 // ---- cubic spline, support q < 1 (Section 2: h is the radius of the
@@ -395,8 +397,17 @@ struct GeomArgs {
   const float *m;
   const float *hf;     // h as float, sorted order
   float4 *pm;          // out: leaf-relative position, mass
+  unsigned *maxout;    // optional out, per box: largest distance outside the top cell (float bits)
 };
 void launch_leaf_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s);
+// After a drift on an unchanged grid: empty every node box, then refill them
+// and the leaf-relative positions (k_leaf_geometry).
+void launch_refresh_geometry(const GeomArgs &a, int n_nodes, cudaStream_t s);
+// kErrHGrid into *status when some box's h_max (1 + 1e-6) + 2 out > its top-cell
+// width (boxout[b]: box b's largest out-of-cell distance, float bits).
+void launch_grid_check(const double *h, int n, const BoxDev *boxes, int nb,
+                       unsigned long long *hext, const unsigned *boxout, int *status,
+                       cudaStream_t s);
 void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s);
 void launch_h_guess(const GeomArgs &a, double n_ngb, double *h, float *hf, cudaStream_t s);
 

@@ -45,7 +45,8 @@ class sph_params(ctypes.Structure):
                 ("h_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("n_split", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mode", ctypes.c_int), ("profile", ctypes.c_int),
-                ("pair_sort", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("pair_sort", ctypes.c_int), ("reuse_grid", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -69,7 +70,9 @@ class sph_stats_t(ctypes.Structure):
                 ("t_sort_ms", ctypes.c_double),
                 ("direct_list_warps", ctypes.c_int32), ("direct_stage_warps", ctypes.c_int32),
                 ("fallback_causes", ctypes.c_int32 * 4),
-                ("tier2_groups", ctypes.c_int32 * 2), ("tier3_entries", ctypes.c_int32 * 2), ("sort_launches", ctypes.c_int64)]
+                ("tier2_groups", ctypes.c_int32 * 2), ("tier3_entries", ctypes.c_int32 * 2),
+                ("sort_launches", ctypes.c_int64), ("reused_steps", ctypes.c_int64),
+                ("redone_steps", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):
@@ -266,7 +269,8 @@ class Context:
     def __init__(self, n_split: int = 64, precision: int = SPH_PREC_FP32,
                  mode: int = SPH_MODE_BATCHED, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
                  h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False,
-                 pair_sort: bool = True, stream=None, device="cuda"):
+                 pair_sort: bool = True, reuse_grid: bool = True, stream=None,
+                 device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -274,6 +278,7 @@ class Context:
         p.n_split, p.precision, p.mode = n_split, precision, mode
         p.profile = int(bool(profile))
         p.pair_sort = int(bool(pair_sort))
+        p.reuse_grid = int(bool(reuse_grid))
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream

@@ -54,10 +54,17 @@ def _check_orders(p, c):
             members0 = members
         for m, m0 in zip(members, members0):
             assert np.array_equal(m, m0), "a leaf holds different particles on another axis"
-        # keys in FP64 from caller positions (a leaf lies inside one box image)
-        key = p.x[order] @ AXES[k]
+        # keys in FP64 from caller positions, each taken at the periodic image
+        # nearest the first particle of its leaf (after steps on a reused grid
+        # a leaf's particles may straddle the box boundary)
         box_of = np.searchsorted(p.box_offsets, order, side="right") - 1
-        tol = 2e-6 * p.box[box_of].max(axis=1)
+        L = p.box[box_of]
+        x = p.x[order]
+        first = x[starts[np.searchsorted(starts, np.arange(n), side="right") - 1]]
+        d = x - first
+        d -= L * np.round(d / L)
+        key = (first + d) @ AXES[k]
+        tol = 2e-6 * L.max(axis=1)
         step = np.diff(key)
         same_leaf = leaf[1:] == leaf[:-1]
         bad = same_leaf & (step < -tol[1:])

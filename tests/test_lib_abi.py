@@ -45,10 +45,11 @@ def test_params_struct_matches_header_defaults(libpath):
     assert p.gamma == pytest.approx(5.0 / 3.0)
     assert p.n_ngb == 48.0 and p.h_tol == 1e-6 and p.max_iter == 30 and p.n_split == 64
     assert p.mode == sph.SPH_MODE_BATCHED and p.precision == sph.SPH_PREC_FP32
-    assert p.pair_sort == 1 and p.profile == 0
+    assert p.pair_sort == 1 and p.profile == 0 and p.reuse_grid == 1
     assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4
-    assert [f for f, _ in sph.sph_params._fields_][-3:] == ["profile", "pair_sort", "reserved"]
-    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 8 * 4 + 8
+    assert [f for f, _ in sph.sph_params._fields_][-4:] == ["profile", "pair_sort", "reuse_grid",
+                                                           "reserved"]
+    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 8 * 4 + 3 * 8
 
 
 def test_param_pair_sort_validated(libpath):
