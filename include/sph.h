@@ -157,6 +157,7 @@ typedef struct {
   int64_t reused_steps;       /* steps run on the previous step's grid (cumulative) */
   int64_t redone_steps;       /* of those, steps redone on a new grid because a particle had
                                  moved too far from its top cell (cumulative) */
+  int64_t graph_steps;        /* of those, steps launched as one CUDA graph (cumulative) */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,

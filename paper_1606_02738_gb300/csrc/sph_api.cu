@@ -87,6 +87,16 @@ struct sph_ctx {
   bool groups_geom_valid = false;  // group frames and boxes match the current positions
   bool grid_reusable = false;      // the last step's grid passed the reach check
   int regrids_in_step = 0;
+  long long grid_stamp = 0;        // bumped by every regrid (sizes, buffers, store swap)
+  // steady steps as one CUDA graph (batched FP32 form on a reused grid)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  long long graph_stamp = -1;
+  long long graph_kernels = 0, graph_dens = 0, graph_force = 0;
+  unsigned graph_stage_mask = 0;   // stages whose events the graph records
+  bool capturing = false;
+  long long graph_steps = 0;
   unsigned *boxout = nullptr;      // per box: largest distance outside the top cell
   int last_passes = 0, last_rebuilds = 0;
   // cumulative counters and stage timers
@@ -94,9 +104,9 @@ struct sph_ctx {
   long long reused_steps = 0, redone_steps = 0;
   unsigned long long total_dens_inter = 0, total_force_inter = 0;
   bool force_pending = false;  // force counters on the device not yet added to the totals
-  cudaEvent_t ev[7][2] = {};
-  bool ev_pending[7] = {};
-  double t_ms[7] = {};
+  cudaEvent_t ev[9][2] = {};
+  bool ev_pending[9] = {};
+  double t_ms[9] = {};
 };
 
 namespace sph {
@@ -105,7 +115,10 @@ thread_local long long *g_launch_count = nullptr;
 
 namespace {
 
-enum Stage { kGrid = 0, kLists, kDens, kGhost, kForce, kInteg, kSort, kNStages };
+// Timed stages. The walks before the density and before the force, and the
+// two kicks, have separate slots so one captured step records each once.
+enum Stage { kGrid = 0, kLists, kDens, kGhost, kForce, kInteg, kSort, kLists2, kInteg2, kNStages };
+static_assert(kNStages == 9, "event arrays of sph_ctx");
 
 // Points the launch counter at this context for the duration of an API call.
 struct LaunchScope {
@@ -114,22 +127,37 @@ struct LaunchScope {
   ~LaunchScope() { g_launch_count = prev; }
 };
 
+// Inside a stream capture an event record must be an external event node to
+// take a timestamp when the graph runs (a plain record only orders streams).
+void record(sph_ctx *c, cudaEvent_t e) {
+  if (c->capturing)
+    cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, c->stream);
+}
 void tic(sph_ctx *c, Stage s) {
-  if (c->p.profile) cudaEventRecord(c->ev[s][0], c->stream);
+  if (c->p.profile) record(c, c->ev[s][0]);
 }
 void toc(sph_ctx *c, Stage s) {
   if (!c->p.profile) return;
-  cudaEventRecord(c->ev[s][1], c->stream);
+  record(c, c->ev[s][1]);
   c->ev_pending[s] = true;
+  if (c->capturing) c->graph_stage_mask |= 1u << s;
 }
 // Add the elapsed time of every bracket whose closing event was recorded.
 void collect_timers(sph_ctx *c) {
   if (!c->p.profile) return;
   for (int s = 0; s < kNStages; ++s) {
     if (!c->ev_pending[s]) continue;
-    if (cudaEventSynchronize(c->ev[s][1]) != cudaSuccess) continue;
+    if (cudaEventSynchronize(c->ev[s][1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[s][0], c->ev[s][1]) == cudaSuccess) c->t_ms[s] += ms;
+    if (cudaEventElapsedTime(&ms, c->ev[s][0], c->ev[s][1]) == cudaSuccess)
+      c->t_ms[s] += ms;
+    else
+      cudaGetLastError();  // a timer is diagnostics: never fail the call over it
     c->ev_pending[s] = false;
   }
 }
@@ -525,6 +553,7 @@ int build_grid_inner(sph_ctx *c, bool from_caller, const float *cv, const float 
   launch_leaf_geometry(ga, n_nodes, c->stream);
   TRY(sync_check(c));
   CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
+  ++c->grid_stamp;
   c->grid_valid = true;
   c->groups_valid = false;
   c->groups_geom_valid = false;
@@ -662,7 +691,8 @@ constexpr int kTaskCap = 384;  // task slots per group
 // Group task lists: one walk, written into fixed per-group slots (no host
 // round trip).
 int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &tasks) {
-  tic(c, kLists);
+  const Stage stage = force ? kLists2 : kLists;
+  tic(c, stage);
   const int ng = c->n_groups;
   TRY(ensure(c, cnt, sizeof(int) * (size_t)std::max(ng, 1)));
   TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(ng, 1) * kTaskCap));
@@ -685,7 +715,7 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &t
   la.walk_queued = &c->ctr->walk_queued;
   CUDA_TRY(cudaMemsetAsync(la.walk_queued, 0, sizeof(int), c->stream));
   launch_group_lists(la, c->stream);
-  toc(c, kLists);
+  toc(c, stage);
   return sync_check(c);
 }
 
@@ -695,7 +725,9 @@ constexpr float kSkinList = 1.05f;   // per-lane list radius = 1.05 x the lane's
 // Batched density: every particle whose group fits the stage and converges
 // inside the kernel is finished here; the rest keep done = 0 for the
 // per-pass loop.
-int density_batched(sph_ctx *c, const float4 *vu_for_P) {
+// The kernels of the batched density (group frames if stale, h maxima, the
+// walk, the three tiers), no host reads.
+int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P) {
   if (!c->groups_valid) TRY(build_groups(c));
   if (!c->groups_geom_valid) {  // positions moved on an unchanged grid
     launch_group_geometry(group_args(c), c->stream);
@@ -742,10 +774,15 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   launch_density_batched(da, c->stream);
   toc(c, kDens);
   ++c->dens_launches;
+  return sync_check(c);
+}
+
+int density_batched(sph_ctx *c, const float4 *vu_for_P) {
+  TRY(enqueue_density_batched(c, vu_for_P));
   TRY(read_counters(c));
   TRY(check_status(c, c->ctr_h->status));
   c->last_passes = c->ctr_h->max_iter_used;
-  return sync_check(c);
+  return SPH_OK;
 }
 
 int density_impl(sph_ctx *c, const float4 *vu_for_P) {
@@ -870,10 +907,8 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
   return SPH_OK;
 }
 
-// Batched force; returns through *all_done whether every particle was
-// finished (else the per-leaf form must run).
-int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
-  *all_done = false;
+// The kernels of the batched force, no host reads.
+int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force) {
   if (!c->groups_valid) TRY(build_groups(c));
   GroupBuildArgs gb = group_args(c);
   launch_group_hmax(gb, c->stream);
@@ -910,11 +945,19 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
   ++c->force_launches;
+  return sync_check(c);
+}
+
+// Batched force; returns through *all_done whether every particle was
+// finished (else the per-leaf form must run).
+int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
+  *all_done = false;
+  TRY(enqueue_force_batched(c, vu_for_force));
   TRY(read_counters(c));
   c->force_pending = true;  // banked by the next read, with any per-leaf remainder
   *all_done = c->ctr_h->unconverged == 0;
   if (*all_done) c->force_valid = true;
-  return sync_check(c);
+  return SPH_OK;
 }
 
 int force_impl(sph_ctx *c, const float4 *vu_for_force) {
@@ -1025,12 +1068,107 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
   }
   TRY(density_impl(c, c->st.vu_pred));
   TRY(force_impl(c, c->st.vu_pred));
-  tic(c, kInteg);
+  tic(c, kInteg2);
   launch_kick(c->st, c->n, dt, c->ctr, c->stream);
-  toc(c, kInteg);
+  toc(c, kInteg2);
   launch_grid_check(c->st.h, c->n, c->boxes_d, c->nb, c->hext, c->boxout, &c->ctr->step_status,
                     c->stream);
   return read_counters(c);
+}
+
+// Everything a step on the reused grid issues in the batched FP32 form, with
+// no host reads: the body of the captured graph. Mirrors step_once(reuse).
+int enqueue_steady_step(sph_ctx *c, double dt) {
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
+  copy_step_state(c, c->st, c->st2);
+  tic(c, kInteg);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+  toc(c, kInteg);
+  tic(c, kGrid);
+  CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
+  GeomArgs ga = geom_args(c);
+  ga.maxout = c->boxout;
+  launch_refresh_geometry(ga, c->n_nodes, c->stream);
+  toc(c, kGrid);
+  launch_h_guess(geom_args(c), c->p.n_ngb, c->st.h, c->hf, c->stream);
+  launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, c->n, c->stream);
+  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
+  launch_group_geometry(group_args(c), c->stream);
+  c->groups_geom_valid = true;
+  TRY(enqueue_density_batched(c, c->st.vu_pred));
+  TRY(enqueue_force_batched(c, c->st.vu_pred));
+  tic(c, kInteg2);
+  launch_kick(c->st, c->n, dt, c->ctr, c->stream);
+  toc(c, kInteg2);
+  launch_grid_check(c->st.h, c->n, c->boxes_d, c->nb, c->hext, c->boxout, &c->ctr->step_status,
+                    c->stream);
+  return sync_check(c);
+}
+
+// Capture the steady step on a private stream (the caller's may be the legacy
+// default stream, which cannot be captured); host-side counters that the
+// capture advanced are taken back and replayed per launch.
+int capture_steady_step(sph_ctx *c, double dt) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  const long long l0 = c->launches, d0 = c->dens_launches, f0 = c->force_launches;
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  c->graph_stage_mask = 0;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? enqueue_steady_step(c, dt) : SPH_OK;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : e;
+  c->capturing = false;
+  c->stream = user;
+  c->graph_kernels = c->launches - l0;
+  c->graph_dens = c->dens_launches - d0;
+  c->graph_force = c->force_launches - f0;
+  c->launches = l0;
+  c->dens_launches = d0;
+  c->force_launches = f0;
+  for (int s = 0; s < kNStages; ++s)  // nothing was recorded yet
+    if (c->graph_stage_mask & (1u << s)) c->ev_pending[s] = false;
+  if (rc || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : fail(c, SPH_ECUDA, "step capture failed: %s", cudaGetErrorString(e2));
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    cudaGetLastError();
+    return fail(c, SPH_ECUDA, "step graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  c->graph_dt = dt;
+  c->graph_stamp = c->grid_stamp;
+  return SPH_OK;
+}
+
+// One steady step as a graph launch, then one read of the counters.
+int graph_step(sph_ctx *c, double dt) {
+  if (!c->graph || c->graph_dt != dt || c->graph_stamp != c->grid_stamp)
+    TRY(capture_steady_step(c, dt));
+  CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+  c->launches += c->graph_kernels;
+  c->dens_launches += c->graph_dens;
+  c->force_launches += c->graph_force;
+  for (int s = 0; s < kNStages; ++s)
+    if (c->graph_stage_mask & (1u << s)) c->ev_pending[s] = true;
+  c->force_pending = true;  // banked by the read below
+  c->regrids_in_step = 0;
+  ++c->graph_steps;
+  TRY(read_counters(c));
+  c->total_dens_inter += c->ctr_h->dens_inter;
+  c->last_passes = c->ctr_h->max_iter_used;
+  c->density_valid = true;
+  c->force_valid = true;
+  return SPH_OK;
 }
 
 }  // namespace
@@ -1174,9 +1312,18 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
     return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
   for (int s = 0; s < n_steps; ++s) {
     const bool reuse = c->p.reuse_grid && c->grid_reusable && c->grid_valid;
-    TRY(step_once(c, dt, reuse));
+    const bool graph = reuse && c->p.mode == SPH_MODE_BATCHED &&
+                       c->p.precision == SPH_PREC_FP32 && c->groups_valid;
+    if (graph)
+      TRY(graph_step(c, dt));
+    else
+      TRY(step_once(c, dt, reuse));
     if (reuse) ++c->reused_steps;
     int st = c->ctr_h->step_status;
+    if (graph) {  // the graph has no per-pass form and no regrid: redo such a step
+      st |= c->ctr_h->status & kErrHGrid;
+      if (c->ctr_h->fallback > 0) st |= kErrHGrid;
+    }
     if ((st & kErrHGrid) && reuse && c->regrids_in_step == 0) {
       ++c->redone_steps;
       // a particle moved too far from its top cell for the h it now has:
@@ -1252,11 +1399,11 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->density_launches = c->dens_launches;
   out->force_launches = c->force_launches;
   out->t_grid_ms = c->t_ms[kGrid];
-  out->t_lists_ms = c->t_ms[kLists];
+  out->t_lists_ms = c->t_ms[kLists] + c->t_ms[kLists2];
   out->t_density_ms = c->t_ms[kDens];
   out->t_ghost_ms = c->t_ms[kGhost];
   out->t_force_ms = c->t_ms[kForce];
-  out->t_integrate_ms = c->t_ms[kInteg];
+  out->t_integrate_ms = c->t_ms[kInteg] + c->t_ms[kInteg2];
   out->t_sort_ms = c->t_ms[kSort];
   out->direct_list_warps = c->ctr_h->direct[0];
   out->direct_stage_warps = c->ctr_h->direct[1];
@@ -1267,6 +1414,7 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   }
   out->sort_launches = c->sort_launches;
   out->reused_steps = c->reused_steps;
+  out->graph_steps = c->graph_steps;
   out->redone_steps = c->redone_steps;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
@@ -1294,6 +1442,8 @@ void sph_destroy(sph_ctx *c) {
   for (auto &pair : c->ev)
     for (auto &e : pair)
       if (e) cudaEventDestroy(e);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 

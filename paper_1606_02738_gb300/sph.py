@@ -72,7 +72,7 @@ class sph_stats_t(ctypes.Structure):
                 ("fallback_causes", ctypes.c_int32 * 4),
                 ("tier2_groups", ctypes.c_int32 * 2), ("tier3_entries", ctypes.c_int32 * 2),
                 ("sort_launches", ctypes.c_int64), ("reused_steps", ctypes.c_int64),
-                ("redone_steps", ctypes.c_int64)]
+                ("redone_steps", ctypes.c_int64), ("graph_steps", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):

@@ -1,5 +1,6 @@
 """Steps on a reused grid (SURVEY's incremental rebuild: the grid of the last
-regrid is kept while every particle stays within reach of its top cell),
+regrid is kept while every particle stays within reach of its top cell; in
+the batched FP32 form such a step is one CUDA graph launch),
 through the C ABI and against the FP64 oracle. A step whose particles moved
 too far is redone from its starting state on a new grid; the results must
 not depend on which path a step took."""
@@ -40,6 +41,10 @@ def test_sod_steps_on_reused_grid_match_oracle(mode):
     g = _steps(p, n, dt, mode=mode)
     st = g["stats"]
     assert st["reused_steps"] >= n - 2, st["reused_steps"]
+    if mode == sph.SPH_MODE_BATCHED:  # steps on a reused grid run as one CUDA graph
+        assert st["graph_steps"] == st["reused_steps"], st["graph_steps"]
+    else:
+        assert st["graph_steps"] == 0
     s = run_oracle(p, steps=n, dt=dt)
     compare_density(g, s, tol_rho=2e-5, tol_h=2e-5, counts=False, check_P=False)
     compare_force(g, s, tol_a=3e-4, tol_du=3e-4)

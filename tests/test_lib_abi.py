@@ -49,7 +49,7 @@ def test_params_struct_matches_header_defaults(libpath):
     assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4
     assert [f for f, _ in sph.sph_params._fields_][-4:] == ["profile", "pair_sort", "reuse_grid",
                                                            "reserved"]
-    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 8 * 4 + 3 * 8
+    assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 8 * 4 + 4 * 8
 
 
 def test_param_pair_sort_validated(libpath):
