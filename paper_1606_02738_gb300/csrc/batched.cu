@@ -876,6 +876,48 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 6 : 1)
   }
 }
 
+// One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
+// particles. hi2 < 0: the entry is a listed neighbour (accepted); otherwise
+// the pair is tested, r > 0 and r^2 < max(h_i^2, h_j^2).
+template <bool KAHAN>
+struct ForceAcc {
+  float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
+  float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;  // Kahan compensations
+  int c = 0;
+  template <class SM>
+  __device__ __forceinline__ void add(const SM &S, int k, const float4 *vu, float px,
+                                      float py, float pz, float4 fi, float4 vi, float hi2) {
+    const float4 q = S.sq[k];
+    const float2 f = S.sf[k];
+    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (hi2 >= 0.f && !(r2 > 0.f && r2 < fmaxf(hi2, f.y))) return;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float ti = fi.z * dw_only(r * fi.y);         // A_i dW/dr(r, h_i)
+    const float tj = f.x * dw_only(r * rsqrtf(f.y));   // A_j dW/dr(r, h_j)
+    const float fac = q.w * (ti + tj) * rinv;
+    const float4 vj = vu[S.sj[k]];
+    const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+    accumulate(fac, dx, dy, dz, q.w * ti * rinv * dvdx);
+  }
+  // a -= fac (x_i - x_j), du/dt += the energy term
+  __device__ __forceinline__ void accumulate(float fac, float dx, float dy, float dz, float dui) {
+    if (KAHAN) {
+      add_comp(ax, cx, -fac * dx);
+      add_comp(ay, cy, -fac * dy);
+      add_comp(az, cz, -fac * dz);
+      add_comp(du, cu, dui);
+    } else {
+      ax = fmaf(-fac, dx, ax);
+      ay = fmaf(-fac, dy, ay);
+      az = fmaf(-fac, dz, az);
+      du += dui;
+    }
+    ++c;
+  }
+};
+
 // ---------------------------------------------------------------- third tier
 //
 // Targets whose group outgrew both stages or its task slots (a large-h
@@ -1113,6 +1155,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_density_stream(BatchDensArgs a
   }
 }
 
+template <bool KAHAN>
 __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a) {
   __shared__ int2 stack[kSWarps][kSStack];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1129,8 +1172,8 @@ __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a)
     float xt[3], p[3];
     target_pos(a.leaves, a.leaf_of, a.pm, G, i, xt, p);
     const float4 fi = a.fi[i], vi = a.vu[i];
-    float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
-    int c = 0, seen = 0;
+    ForceAcc<KAHAN> acc;
+    int seen = 0;
     const bool ok = walk_stream<true>(
         a.nodes, a.leaves, a.pm, B, G, xt, fi.x, lane, stack[warp],
         [&](float4 q, int j) {
@@ -1147,21 +1190,16 @@ __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a)
           const float fac = q.w * (ti + tj) * rinv;
           const float4 vj = a.vu[j];
           const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-          ax = fmaf(-fac, dx, ax);
-          ay = fmaf(-fac, dy, ay);
-          az = fmaf(-fac, dz, az);
-          du = fmaf(q.w * ti * rinv, dvdx, du);
-          ++c;
+          acc.accumulate(fac, dx, dy, dz, q.w * ti * rinv * dvdx);
         });
     ntest += seen;
     if (!ok) {  // left to the per-pass form
       if (lane == 0) ++fallback;
       continue;
     }
-    ax = warp_sum_f(ax);
-    ay = warp_sum_f(ay);
-    az = warp_sum_f(az);
-    du = warp_sum_f(du);
+    const float ax = warp_sum_f(acc.ax), ay = warp_sum_f(acc.ay), az = warp_sum_f(acc.az),
+                du = warp_sum_f(acc.du);
+    int c = acc.c;
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) {
       a.acc[i] = make_float4(ax, ay, az, du);
@@ -1216,36 +1254,8 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   note_launch();
 }
 
-// One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
-// particles. hi2 < 0: the entry is a listed neighbour (accepted); otherwise
-// the pair is tested, r > 0 and r^2 < max(h_i^2, h_j^2).
-struct ForceAcc {
-  float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
-  int c = 0;
-  template <class SM>
-  __device__ __forceinline__ void add(const SM &S, int k, const float4 *vu, float px,
-                                      float py, float pz, float4 fi, float4 vi, float hi2) {
-    const float4 q = S.sq[k];
-    const float2 f = S.sf[k];
-    const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (hi2 >= 0.f && !(r2 > 0.f && r2 < fmaxf(hi2, f.y))) return;
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float ti = fi.z * dw_only(r * fi.y);         // A_i dW/dr(r, h_i)
-    const float tj = f.x * dw_only(r * rsqrtf(f.y));   // A_j dW/dr(r, h_j)
-    const float fac = q.w * (ti + tj) * rinv;
-    const float4 vj = vu[S.sj[k]];
-    const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-    ax = fmaf(-fac, dx, ax);
-    ay = fmaf(-fac, dy, ay);
-    az = fmaf(-fac, dz, az);
-    du = fmaf(q.w * ti * rinv, dvdx, du);
-    ++c;
-  }
-};
 
-template <int NS>
+template <bool KAHAN, int NS>
 __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
     k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1328,7 +1338,7 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
       if (__any_sync(0xffffffffu, cnt > kLaneF)) mode = 1;
       __syncwarp();
     }
-    ForceAcc acc;
+    ForceAcc<KAHAN> acc;
     if (mode == 0) {
       const int tmax = warp_max_int(has ? cnt : 0);
       for (int t = 0; t < tmax; ++t)
@@ -1370,15 +1380,16 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
 
 }
 
-template <int NS>
+template <bool KAHAN, int NS>
 void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
   const int bytes = (int)sizeof(ForceSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_force_batched<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_force_batched<KAHAN, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
     attr = true;
   }
-  k_force_batched<NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
+  k_force_batched<KAHAN, NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
 }
 
@@ -1386,9 +1397,15 @@ void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
   const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
-  launch_force_tier<kStageF>(a, 0, blocks, s);
-  launch_force_tier<kBigStageF>(a, 1, big, s);
-  k_force_stream<<<152 * 8, 128, 0, s>>>(a);
+  if (a.kahan) {
+    launch_force_tier<true, kStageF>(a, 0, blocks, s);
+    launch_force_tier<true, kBigStageF>(a, 1, big, s);
+    k_force_stream<true><<<152 * 8, 128, 0, s>>>(a);
+  } else {
+    launch_force_tier<false, kStageF>(a, 0, blocks, s);
+    launch_force_tier<false, kBigStageF>(a, 1, big, s);
+    k_force_stream<false><<<152 * 8, 128, 0, s>>>(a);
+  }
   note_launch();
 }
 

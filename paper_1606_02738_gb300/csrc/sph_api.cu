@@ -941,6 +941,7 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force) {
   fa.gpos = c->gpos;
   fa.nodes = as<Node>(c->nodes);
   fa.boxes = c->boxes_d;
+  fa.kahan = c->p.precision == SPH_PREC_KAHAN;
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -966,7 +967,7 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   const int *active = nullptr;
   int n_targets = c->n_leaves;
   const unsigned char *skip = nullptr;
-  if (c->p.mode == SPH_MODE_BATCHED && c->p.precision == SPH_PREC_FP32) {
+  if (c->p.mode == SPH_MODE_BATCHED) {
     bool all = false;
     TRY(force_batched(c, vu_for_force, &all));
     if (all) return SPH_OK;
@@ -1312,8 +1313,7 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
     return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
   for (int s = 0; s < n_steps; ++s) {
     const bool reuse = c->p.reuse_grid && c->grid_reusable && c->grid_valid;
-    const bool graph = reuse && c->p.mode == SPH_MODE_BATCHED &&
-                       c->p.precision == SPH_PREC_FP32 && c->groups_valid;
+    const bool graph = reuse && c->p.mode == SPH_MODE_BATCHED && c->groups_valid;
     if (graph)
       TRY(graph_step(c, dt));
     else

@@ -613,6 +613,7 @@ struct BatchForceArgs {
   int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
   const Node *nodes;     // the third tier walks the octrees itself
   const BoxDev *boxes;
+  int kahan;             // compensated sums
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 
