@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--mode", choices=["plain", "batched"], default="batched")
     ap.add_argument("--no-pair-sort", action="store_true",
                     help="per-pass form without the pair-axis sorts (whole source leaves)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the library's autotuner (tile, n_split, cell_factor) before timing")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other interaction form for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -308,6 +310,7 @@ def run_ours(args, d: Dist):
     ctx.load(p)
     ctx.density()
     ctx.force()
+    tuned = None if args.no_autotune else ctx.autotune()  # untimed set-up
     if dt is None:
         dt = cfl_dt(ctx, p.gamma)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
@@ -416,6 +419,7 @@ def run_ours(args, d: Dist):
         oc.load(p)
         oc.density()
         oc.force()
+        otuned = None if args.no_autotune else oc.autotune()
         for _ in range(args.warmup):
             oc.step(dt, 1)
         torch.cuda.synchronize(dev)
@@ -433,6 +437,7 @@ def run_ours(args, d: Dist):
         ointer = (o1["total_density_interactions"] - o0["total_density_interactions"] +
                   o1["total_force_interactions"] - o0["total_force_interactions"])
         other = {"mode": "plain" if omode == sph.SPH_MODE_PLAIN else "batched",
+                 "autotune": otuned,
                  "value": ointer / (oms / 1000.0), "ms_per_step": oms / args.steps,
                  "interactions_per_step": ointer / args.steps}
         oc.close()
@@ -465,6 +470,7 @@ def run_ours(args, d: Dist):
                        "direct_warps_last_step": [s1["direct_list_warps"],
                                                   s1["direct_stage_warps"]],
                        "pair_sort": not args.no_pair_sort,
+                       "autotune": tuned,
                        "leaves": s1["n_leaves"]},
             "roofline": roof,
             "stage_ms_per_step": stages,

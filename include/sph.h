@@ -97,7 +97,10 @@ typedef struct {
                       outside its cell <= the cell width), refreshing positions and boxes
                       only, and runs those steps as one CUDA graph in the batched FP32
                       form; 0: regrid every step (same results up to summation order) */
-  int reserved[1]; /* zero */
+  int tile;        /* batched first-tier stage: 0 small (more blocks per SM), 1 large
+                      (fewer groups to the second tier on clumped inputs) */
+  double cell_factor; /* top-cell edge >= cell_factor x the largest h where the box allows
+                         (1 <= cell_factor <= 4; >= 1 x always) */
 } sph_params;
 
 typedef struct {
@@ -161,7 +164,8 @@ typedef struct {
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,
- * n_split = 64, FP32, batched mode, pair sorts on, grid reuse on, profiling off. */
+ * n_split = 64, FP32, batched mode, pair sorts on, grid reuse on, profiling
+ * off, tile 0, cell_factor 2. */
 void sph_default_params(sph_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a
@@ -213,6 +217,19 @@ int sph_step(sph_ctx *ctx, double dt, int n_steps);
  * at the field). Asynchronous. Errors: SPH_EINVAL (unknown field / null),
  * SPH_ESTATE (field not computed yet). */
 int sph_get(sph_ctx *ctx, int field, void *dev_out);
+
+/* Autotuner (no counterpart in the paper; the paper tunes its cell split
+ * threshold by hand, Section 3.1). On the loaded state, times one
+ * sph_density + sph_force for every combination of tile (0, 1; batched form
+ * only), n_split (16, 32, 64, 128) and cell_factor (1.5, 2, 2.5, 3), each on its own
+ * grid, best of 2, and keeps the fastest in the context's parameters; then
+ * rebuilds the grid and leaves density and force computed on the current
+ * state. Results do not depend on these parameters beyond summation order.
+ * Outputs (host pointers, each may be NULL): the chosen tile, n_split,
+ * cell_factor, and the best time in ms. Synchronises. Errors: SPH_ESTATE
+ * before sph_init, or those of sph_density / sph_force. */
+int sph_autotune(sph_ctx *ctx, int *tile_out, int *n_split_out, double *cell_factor_out,
+                 double *ms_out);
 
 /* Pair-axis sort of the current grid along direction `axis` (0..12; the
  * integer offsets (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1)

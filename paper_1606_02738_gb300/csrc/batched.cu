@@ -413,6 +413,14 @@ constexpr int kBigStageD = 4096; // second tier: groups whose stage overflowed t
 constexpr int kBigStageF = 3072;
 constexpr int kCandD = 1152;     // density entries kept per warp
 constexpr int kCandF = 512;      // force entries kept per warp
+// Tile 1 (the autotuner's alternative for clumped inputs): larger first-tier
+// stages at lower occupancy, so fewer groups need the second tier.
+constexpr int kStageDL = 1792;   // 4 blocks per SM
+constexpr int kStageFL = 1024;   // 5 blocks per SM
+constexpr int kCandFL = 640;
+constexpr int dens_min_blocks(int ns) { return ns == kStageD ? 6 : (ns == kStageDL ? 4 : 1); }
+constexpr int force_min_blocks(int ns) { return ns == kStageF ? 7 : (ns == kStageFL ? 5 : 1); }
+constexpr int force_cand(int ns) { return ns == kStageF ? kCandF : kCandFL; }
 constexpr int kLaneD = 32;       // density list entries per lane
 constexpr int kLaneF = 28;       // force list entries per lane
 
@@ -431,7 +439,7 @@ struct ForceSmem {
   float4 sq[NS];                            // position in the group frame, m
   float2 sf[NS];                            // A (8/pi) h^-4, h^2
   int sj[NS];                               // particle index (velocity read on use)
-  unsigned short cand[kNW][kCandF];
+  unsigned short cand[kNW][force_cand(NS)];
   unsigned short list[kNW][kLaneF * 32];
   int wcount[kNW];
 };
@@ -464,9 +472,11 @@ struct StageRange {
 };
 
 constexpr int kMap = 1024;  // per-warp particle -> task map (bytes, aliases the warp's cand)
-static_assert(kCandD * 2 >= kMap && kCandF * 2 >= kMap, "task map must fit a warp's cand");
+static_assert(kCandD * 2 >= kMap && kCandF * 2 >= kMap && kCandFL * 2 >= kMap,
+              "task map must fit a warp's cand");
 static_assert(kStageD % kNW == 0 && kStageF % kNW == 0 && kBigStageD % kNW == 0 &&
-                  kBigStageF % kNW == 0, "stage segments");
+                  kBigStageF % kNW == 0 && kStageDL % kNW == 0 && kStageFL % kNW == 0,
+              "stage segments");
 
 // Stage the particles of this warp's share of the group's source leaves that
 // lie within R of the group box (R = Rg, or max(Rg, h_j) for the force), in
@@ -689,11 +699,11 @@ struct DensAcc {
 };
 
 template <bool KAHAN, int NS>
-__global__ void __launch_bounds__(kNW * 32, NS == kStageD ? 6 : 1)
+__global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
-  constexpr bool TIGHT = NS != kStageD;  // the second tier stages by each target's radius
+  constexpr bool TIGHT = NS == kBigStageD;  // the second tier stages by each target's radius
   const double tol_n = a.tol * a.n_ngb;
   const float gm1 = (float)(a.gamma - 1.0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1243,11 +1253,17 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
   if (a.kahan) {
-    launch_density_tier<true, kStageD>(a, 0, blocks, s);
+    if (a.tile)
+      launch_density_tier<true, kStageDL>(a, 0, blocks, s);
+    else
+      launch_density_tier<true, kStageD>(a, 0, blocks, s);
     launch_density_tier<true, kBigStageD>(a, 1, big, s);
     k_density_stream<true><<<152 * 8, 128, 0, s>>>(a);
   } else {
-    launch_density_tier<false, kStageD>(a, 0, blocks, s);
+    if (a.tile)
+      launch_density_tier<false, kStageDL>(a, 0, blocks, s);
+    else
+      launch_density_tier<false, kStageD>(a, 0, blocks, s);
     launch_density_tier<false, kBigStageD>(a, 1, big, s);
     k_density_stream<false><<<152 * 8, 128, 0, s>>>(a);
   }
@@ -1256,11 +1272,12 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
 
 
 template <bool KAHAN, int NS>
-__global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
+__global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
-  constexpr bool TIGHT = NS != kStageF;  // the second tier stages by each target's radius
+  constexpr bool TIGHT = NS == kBigStageF;  // the second tier stages by each target's radius
+  constexpr int CANDF = force_cand(NS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
@@ -1314,11 +1331,11 @@ __global__ void __launch_bounds__(kNW * 32, NS == kStageF ? 7 : 1)
     sub_box(has, px, py, pz, blo, bhi);
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-    const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, kCandF, lane);
+    const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, CANDF, lane);
     // 0: per-lane lists; 1: a list outgrew kLaneF, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandF, it reads the
     // whole stage (ncand is warp-uniform)
-    int mode = ncand > kCandF ? 2 : 0;
+    int mode = ncand > CANDF ? 2 : 0;
     const float hi2 = has ? fi.w : -1.f;
     int cnt = 0;
     if (mode == 0) {
@@ -1398,11 +1415,17 @@ void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
   const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
   if (a.kahan) {
-    launch_force_tier<true, kStageF>(a, 0, blocks, s);
+    if (a.tile)
+      launch_force_tier<true, kStageFL>(a, 0, blocks, s);
+    else
+      launch_force_tier<true, kStageF>(a, 0, blocks, s);
     launch_force_tier<true, kBigStageF>(a, 1, big, s);
     k_force_stream<true><<<152 * 8, 128, 0, s>>>(a);
   } else {
-    launch_force_tier<false, kStageF>(a, 0, blocks, s);
+    if (a.tile)
+      launch_force_tier<false, kStageFL>(a, 0, blocks, s);
+    else
+      launch_force_tier<false, kStageF>(a, 0, blocks, s);
     launch_force_tier<false, kBigStageF>(a, 1, big, s);
     k_force_stream<false><<<152 * 8, 128, 0, s>>>(a);
   }

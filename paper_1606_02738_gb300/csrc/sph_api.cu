@@ -372,8 +372,9 @@ double bits_to_double(unsigned long long b) {
   return d;
 }
 
-// Choose top-grid cells per box from the largest h: edge >= 2 h_max where
-// the box allows (headroom for h growth), never below h_max, >= 3 per axis.
+// Choose top-grid cells per box from the largest h: edge >= cell_factor h_max
+// where the box allows (headroom for h growth and for drift on a reused
+// grid), never below h_max, >= 3 per axis.
 int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
   int base = 0;
   for (int b = 0; b < c->nb; ++b) {
@@ -399,7 +400,7 @@ int choose_grid(sph_ctx *c, const std::vector<double> &hmax_box) {
                   lmin / 3.0);
     const int64_t cap = std::max<int64_t>(27, 2 * (int64_t)B.count);
     for (int d = 0; d < 3; ++d) {
-      int64_t nd = (int64_t)std::floor(B.L[d] / (2.0 * hm));
+      int64_t nd = (int64_t)std::floor(B.L[d] / (c->p.cell_factor * hm));
       if (nd < 3) nd = (int64_t)std::floor(B.L[d] / hm);
       nd = std::max<int64_t>(3, std::min<int64_t>(nd, 1024));
       B.n[d] = (int)nd;
@@ -769,6 +770,7 @@ int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P) {
   da.queue = as<int>(c->gqueue);  // ctr->queued, queued2 were zeroed with the counters
   da.queue2 = as<int>(c->gqueue) + c->n_groups;
   da.gpos = c->gpos;
+  da.tile = c->p.tile;
   da.nodes = as<Node>(c->nodes);
   tic(c, kDens);
   launch_density_batched(da, c->stream);
@@ -939,6 +941,7 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force) {
   fa.queue = as<int>(c->gqueue);
   fa.queue2 = as<int>(c->gqueue) + c->n_groups;
   fa.gpos = c->gpos;
+  fa.tile = c->p.tile;
   fa.nodes = as<Node>(c->nodes);
   fa.boxes = c->boxes_d;
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
@@ -1188,6 +1191,8 @@ void sph_default_params(sph_params *p) {
   p->mode = SPH_MODE_BATCHED;
   p->pair_sort = 1;
   p->reuse_grid = 1;
+  p->tile = 0;
+  p->cell_factor = 2.0;
 }
 
 int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
@@ -1200,7 +1205,8 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       q.n_split < 8 || q.n_split > 256 ||
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
-      (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1))
+      (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
+      (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0))
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;
@@ -1355,6 +1361,66 @@ int sph_get(sph_ctx *c, int field, void *dev_out) {
     return fail(c, SPH_ESTATE, "field %d needs sph_force on the current state", field);
   launch_get(field, dev_out, c->st.orig, c->n, c->st, c->rho, c->omega, c->P, c->nngb, c->niter,
              c->nforce, c->stream);
+  return sync_check(c);
+}
+
+int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_factor_out,
+                 double *ms_out) {
+  if (!c) return SPH_EINVAL;
+  LaunchScope ls(c);
+  c->err.clear();
+  if (!c->loaded) return fail(c, SPH_ESTATE, "sph_autotune before sph_init");
+  const sph_params keep = c->p;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, SPH_ECUDA, "event creation failed");
+  }
+  const int tiles = c->p.mode == SPH_MODE_BATCHED ? 2 : 1;
+  const int splits[] = {16, 32, 64, 128};
+  const double factors[] = {1.5, 2.0, 2.5, 3.0};
+  double best = 1e300;
+  sph_params best_p = keep;
+  int rc = density_impl(c, c->st.vu);  // converged h to start from
+  for (int t = 0; t < tiles && rc == SPH_OK; ++t)
+    for (int ns : splits)
+      for (double cf : factors) {
+        if (rc != SPH_OK) break;
+        c->p.tile = t;
+        c->p.n_split = ns;
+        c->p.cell_factor = cf;
+        c->grid_valid = false;
+        rc = build_grid(c, false, nullptr, nullptr, nullptr, nullptr);
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 2 && rc == SPH_OK; ++rep) {
+          cudaEventRecord(e0, c->stream);
+          rc = density_impl(c, c->st.vu);
+          if (rc == SPH_OK) rc = force_impl(c, c->st.vu);
+          cudaEventRecord(e1, c->stream);
+          if (rc == SPH_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms_min = std::min(ms_min, (double)ms);
+          }
+        }
+        if (rc == SPH_OK && ms_min < best) {
+          best = ms_min;
+          best_p = c->p;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->p = rc == SPH_OK ? best_p : keep;
+  c->grid_valid = false;  // rebuild the grid with the chosen parameters
+  c->grid_reusable = false;
+  if (rc != SPH_OK) return rc;
+  TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
+  TRY(density_impl(c, c->st.vu));
+  TRY(force_impl(c, c->st.vu));
+  if (tile_out) *tile_out = c->p.tile;
+  if (n_split_out) *n_split_out = c->p.n_split;
+  if (cell_factor_out) *cell_factor_out = c->p.cell_factor;
+  if (ms_out) *ms_out = best;
   return sync_check(c);
 }
 

@@ -590,6 +590,7 @@ struct BatchDensArgs {
   int *queue;            // [n_groups] groups handed to the second tier
   int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
   const Node *nodes;     // the third tier walks the octrees itself
+  int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 
@@ -614,6 +615,7 @@ struct BatchForceArgs {
   const Node *nodes;     // the third tier walks the octrees itself
   const BoxDev *boxes;
   int kahan;             // compensated sums
+  int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 

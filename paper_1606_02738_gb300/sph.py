@@ -46,7 +46,7 @@ class sph_params(ctypes.Structure):
                 ("n_split", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mode", ctypes.c_int), ("profile", ctypes.c_int),
                 ("pair_sort", ctypes.c_int), ("reuse_grid", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("tile", ctypes.c_int), ("cell_factor", ctypes.c_double)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -114,6 +114,7 @@ def lib(build_if_needed: bool = True):
         L.sph_step.argtypes = [P, D, I]
         L.sph_get.argtypes = [P, I, P]
         L.sph_get_pair_order.argtypes = [P, I, P, P]
+        L.sph_autotune.argtypes = [P, P, P, P, P]
         L.sph_stats.argtypes = [P, ctypes.POINTER(sph_stats_t)]
         L.sph_last_error.argtypes = [P]
         L.sph_last_error.restype = ctypes.c_char_p
@@ -121,7 +122,7 @@ def lib(build_if_needed: bool = True):
         L.sph_destroy.restype = None
         for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
                   "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
-                  "sph_stats"):
+                  "sph_autotune", "sph_stats"):
             getattr(L, f).restype = I
         _lib = L
         return L
@@ -216,6 +217,16 @@ def sph_get_pair_order(ctx, axis: int, order_out, leaf_out) -> None:
     _check(ctx, lib().sph_get_pair_order(ctx, int(axis), ctypes.c_void_p(_ptr(order_out)),
                                          ctypes.c_void_p(_ptr(leaf_out))),
            "sph_get_pair_order")
+
+
+def sph_autotune(ctx) -> dict:
+    """Runs the library's autotuner on the loaded state; returns its choice."""
+    tile, ns = ctypes.c_int(), ctypes.c_int()
+    cf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().sph_autotune(ctx, ctypes.byref(tile), ctypes.byref(ns), ctypes.byref(cf),
+                                   ctypes.byref(ms)), "sph_autotune")
+    return {"tile": tile.value, "n_split": ns.value, "cell_factor": cf.value,
+            "best_ms": ms.value}
 
 
 def sph_stats(ctx) -> dict:
@@ -326,6 +337,9 @@ class Context:
         out = self.torch.empty(shape, dtype=getattr(self.torch, dtype), device=self.device)
         sph_get(self.ctx, f, out)
         return out
+
+    def autotune(self) -> dict:
+        return sph_autotune(self.ctx)
 
     def pair_order(self, axis: int):
         """(order, leaf) int32 tensors of the pair-axis sort along `axis`."""

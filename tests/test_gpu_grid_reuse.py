@@ -80,3 +80,23 @@ def test_fast_particles_force_a_redo_and_still_match_oracle():
     s = run_oracle(p, steps=n, dt=dt)
     compare_density(g, s, tol_rho=2e-5, tol_h=2e-5, counts=False, check_P=False)
     compare_force(g, s, tol_a=3e-4, tol_du=3e-4)
+
+
+@pytest.mark.parametrize("mode", [sph.SPH_MODE_BATCHED, sph.SPH_MODE_PLAIN])
+def test_autotune_choice_keeps_oracle_results(mode):
+    """The autotuner times density + force for each (tile, n_split,
+    cell_factor) and keeps the fastest; results must not change."""
+    p = inputs.clustered(30011, n_spheres=8, seed=71, sigma_v=0.2)
+    c = sph.Context(mode=mode).load(p)
+    choice = c.autotune()
+    assert choice["tile"] in (0, 1) and choice["n_split"] in (16, 32, 64, 128)
+    assert choice["cell_factor"] in (1.5, 2.0, 2.5, 3.0) and choice["best_ms"] > 0
+    if mode == sph.SPH_MODE_PLAIN:
+        assert choice["tile"] == 0
+    g = {k: c.get(k).cpu().numpy() for k in ("h", "rho", "omega", "P", "a", "dudt", "nngb",
+                                              "nforce")}
+    c.step(1e-4, 2)  # the tuned grid steps as well
+    c.close()
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)

@@ -20,7 +20,7 @@ def test_header_declares_the_boundary():
     names = sph.header_functions()
     for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
               "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
-              "sph_stats", "sph_last_error", "sph_destroy", "sph_default_params"):
+              "sph_autotune", "sph_stats", "sph_last_error", "sph_destroy", "sph_default_params"):
         assert f in names
 
 
@@ -46,9 +46,10 @@ def test_params_struct_matches_header_defaults(libpath):
     assert p.n_ngb == 48.0 and p.h_tol == 1e-6 and p.max_iter == 30 and p.n_split == 64
     assert p.mode == sph.SPH_MODE_BATCHED and p.precision == sph.SPH_PREC_FP32
     assert p.pair_sort == 1 and p.profile == 0 and p.reuse_grid == 1
-    assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4
-    assert [f for f, _ in sph.sph_params._fields_][-4:] == ["profile", "pair_sort", "reuse_grid",
-                                                           "reserved"]
+    assert p.tile == 0 and p.cell_factor == 2.0
+    assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4 + 8
+    assert [f for f, _ in sph.sph_params._fields_][-5:] == ["profile", "pair_sort", "reuse_grid",
+                                                           "tile", "cell_factor"]
     assert ctypes.sizeof(sph.sph_stats_t) == 10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 + 2 * 4 + 8 * 4 + 4 * 8
 
 
