@@ -51,6 +51,8 @@ def parse():
                     help="per-pass form without the pair-axis sorts (whole source leaves)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the library's autotuner (tile, n_split, cell_factor) before timing")
+    ap.add_argument("--tune", default=None,
+                    help="fixed 'tile,n_split,cell_factor' instead of the autotuner (profiling runs)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other interaction form for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -306,11 +308,18 @@ def run_ours(args, d: Dist):
     p, dt, wname = workload(args.workload, args.scale)
     mode = sph.SPH_MODE_BATCHED if args.mode == "batched" else sph.SPH_MODE_PLAIN
     stream = torch.cuda.current_stream(dev)
-    ctx = sph.Context(mode=mode, profile=True, pair_sort=not args.no_pair_sort, device=dev)
+    fixed = {}
+    if args.tune:
+        t, ns, cf = args.tune.split(",")
+        fixed = {"tile": int(t), "n_split": int(ns), "cell_factor": float(cf)}
+    ctx = sph.Context(mode=mode, profile=True, pair_sort=not args.no_pair_sort, device=dev,
+                      **fixed)
     ctx.load(p)
     ctx.density()
     ctx.force()
-    tuned = None if args.no_autotune else ctx.autotune()  # untimed set-up
+    tuned = None if (args.no_autotune or fixed) else ctx.autotune()  # untimed set-up
+    if fixed:
+        tuned = dict(fixed, fixed=True)
     if dt is None:
         dt = cfl_dt(ctx, p.gamma)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
