@@ -416,20 +416,24 @@ constexpr int kCandF = 512;      // force entries kept per warp
 // Tile 1 (the autotuner's alternative for clumped inputs): larger first-tier
 // stages at lower occupancy, so fewer groups need the second tier.
 constexpr int kStageDL = 1792;   // 4 blocks per SM
-constexpr int kStageFL = 1024;   // 5 blocks per SM
+constexpr int kStageFL = 1536;   // 4 blocks per SM
 constexpr int kCandFL = 640;
 constexpr int dens_min_blocks(int ns) { return ns == kStageD ? 6 : (ns == kStageDL ? 4 : 1); }
-constexpr int force_min_blocks(int ns) { return ns == kStageF ? 7 : (ns == kStageFL ? 5 : 1); }
+constexpr int force_min_blocks(int ns) { return ns == kStageF ? 7 : (ns == kStageFL ? 4 : 1); }
 constexpr int force_cand(int ns) { return ns == kStageF ? kCandF : kCandFL; }
-constexpr int kLaneD = 32;       // density list entries per lane
-constexpr int kLaneF = 28;       // force list entries per lane
+constexpr int kLaneD = 32;       // density list entries per lane (tile 0)
+constexpr int kLaneF = 28;       // force list entries per lane (tile 0)
+// list entries per lane for a first-tier stage size (tile 1 and the second
+// tier hold longer lists: clumped inputs put more particles inside 1.05 h)
+constexpr int dens_lane(int ns) { return ns == kStageD ? kLaneD : 48; }
+constexpr int force_lane(int ns) { return ns == kStageF ? kLaneF : 32; }
 
 template <int NS>
 struct DensSmem {
   float4 tgt[32];                           // tight stage: target position (group frame), radius
   float4 stage[NS];                         // position in the group frame, m
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
-  unsigned short list[kNW][kLaneD * 32];     // [entry][lane]
+  unsigned short list[kNW][dens_lane(NS) * 32];  // [entry][lane]
   int wcount[kNW];
 };
 
@@ -440,7 +444,7 @@ struct ForceSmem {
   float2 sf[NS];                            // A (8/pi) h^-4, h^2
   int sj[NS];                               // particle index (velocity read on use)
   unsigned short cand[kNW][force_cand(NS)];
-  unsigned short list[kNW][kLaneF * 32];
+  unsigned short list[kNW][force_lane(NS) * 32];
   int wcount[kNW];
 };
 
@@ -704,6 +708,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
   constexpr bool TIGHT = NS == kBigStageD;  // the second tier stages by each target's radius
+  constexpr int LANE = dens_lane(NS);
   const double tol_n = a.tol * a.n_ngb;
   const float gm1 = (float)(a.gamma - 1.0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     sub_box(has, px, py, pz, blo, bhi);
 
     bool failed = false, fin = !has, need_list = has, need_filter = true;
-    // 0: per-lane lists; 1: a lane's list outgrew kLaneD, the warp reads its
+    // 0: per-lane lists; 1: a lane's list outgrew LANE, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandD, the warp reads
     // the whole stage (slower, same sums)
     int mode = 0;
@@ -796,12 +801,12 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
           const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           if (r2 < rl2) {
-            if (cnt < kLaneD) list[cnt * 32 + lane] = (unsigned short)k;
+            if (cnt < LANE) list[cnt * 32 + lane] = (unsigned short)k;
             ++cnt;
           }
         }
         need_list = false;
-        if (__any_sync(0xffffffffu, cnt > kLaneD)) mode = 1;
+        if (__any_sync(0xffffffffu, cnt > LANE)) mode = 1;
         __syncwarp();
       }
       // partial sums over this lane's slice at the current h
@@ -1278,6 +1283,7 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
   constexpr bool TIGHT = NS == kBigStageF;  // the second tier stages by each target's radius
   constexpr int CANDF = force_cand(NS);
+  constexpr int LANE = force_lane(NS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = lane & (kSlice - 1);
   unsigned short *cand = S.cand[warp];
@@ -1332,7 +1338,7 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
     const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, CANDF, lane);
-    // 0: per-lane lists; 1: a list outgrew kLaneF, the warp reads its
+    // 0: per-lane lists; 1: a list outgrew LANE, the warp reads its
     // candidates directly; 2: the candidates outgrew kCandF, it reads the
     // whole stage (ncand is warp-uniform)
     int mode = ncand > CANDF ? 2 : 0;
@@ -1347,12 +1353,12 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
         const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-          if (cnt < kLaneF) list[cnt * 32 + lane] = (unsigned short)k;
+          if (cnt < LANE) list[cnt * 32 + lane] = (unsigned short)k;
           ++cnt;
         }
       }
       if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
-      if (__any_sync(0xffffffffu, cnt > kLaneF)) mode = 1;
+      if (__any_sync(0xffffffffu, cnt > LANE)) mode = 1;
       __syncwarp();
     }
     ForceAcc<KAHAN> acc;
