@@ -228,6 +228,46 @@ def source_sha(files) -> str:
     return h.hexdigest()[:16]
 
 
+def time_per_box(p, dt, args, dev, stream, flush, tuned, sph, torch):
+    """The batched-boxes workload with one context per box: each box's step is
+    its own launch sequence (and graph), the boxes one after another, timed
+    with the same protocol as the single context holding all boxes."""
+    kw = {}
+    if tuned:
+        kw = {k: tuned[k] for k in ("tile", "n_split", "cell_factor")}
+    ctxs = []
+    for b in range(p.n_boxes):
+        c = sph.Context(mode=sph.SPH_MODE_BATCHED, device=dev, **kw).load(p.subset_box(b))
+        c.density()
+        c.force()
+        ctxs.append(c)
+    for _ in range(args.warmup):
+        for c in ctxs:
+            c.step(dt, 1)
+    torch.cuda.synchronize(dev)
+    s0 = [c.stats() for c in ctxs]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        for c in ctxs:
+            c.step(dt, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    s1 = [c.stats() for c in ctxs]
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    inter = sum(b["total_density_interactions"] - a["total_density_interactions"] +
+                b["total_force_interactions"] - a["total_force_interactions"]
+                for a, b in zip(s0, s1))
+    launches = sum(b["kernel_launches"] - a["kernel_launches"] for a, b in zip(s0, s1))
+    for c in ctxs:
+        c.close()
+    return {"contexts": p.n_boxes, "value": inter / (ms / 1000.0), "ms_per_step": ms / args.steps,
+            "interactions_per_step": inter / args.steps,
+            "kernel_launches_per_step": launches / args.steps}
+
+
 # ------------------------------------------------------------ CPU oracle
 
 def cpu_baseline(p, min_s: float = 10.0, max_reps: int = 20) -> dict:
@@ -249,7 +289,47 @@ def cpu_baseline(p, min_s: float = 10.0, max_reps: int = 20) -> dict:
     return {"value": inter / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{reps} h-iterated density + force evaluations of all {p.n} particles "
                       f"of the initial state ({inter} interactions, {dt:.2f} s)",
-            "seconds": dt}
+            "seconds": dt, "single_core": cpu_single_core(p)}
+
+
+_ONE_CORE = r"""
+import sys, time, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_1606_02738_gb300 import inputs
+p = inputs.config(int(sys.argv[2]), float(sys.argv[3]))
+s = oracle.State.from_particles(p)
+oracle.compute_density(s)
+rng = np.random.default_rng(11)
+sub = np.sort(rng.choice(p.n, size=min(int(sys.argv[4]), p.n), replace=False))
+t0 = time.perf_counter()
+d = oracle.density(s.x, s.m, s.box[0], s.h, s.n_ngb, subset=sub)
+f = oracle.force(s.x, s.v, s.m, s.u, s.h, s.rho, s.omega, s.box[0], s.gamma, subset=sub)
+dt = time.perf_counter() - t0
+print(json.dumps({"inter": int(d["count"][sub].sum() + f["count"][sub].sum()), "seconds": dt,
+                  "threads": oracle.num_threads(), "n_sub": int(sub.size)}))
+"""
+
+
+def cpu_single_core(p, n_sub: int = 10000, scale: float = 0.1):
+    """The oracle on one host core (OMP_NUM_THREADS=1, a fresh process): h-iterated
+    density + force of a seeded subset of a Sod tube shrunk by `scale` (same recipe,
+    same per-particle work), with the full neighbour context (the set-up density
+    of all its particles is untimed)."""
+    if p.name != "cfg2_sod":
+        return None
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", _ONE_CORE, ROOT, "2", str(scale), str(n_sub)],
+                             env=env, capture_output=True, text=True, timeout=600, check=True)
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": r["inter"] / r["seconds"], "unit": UNIT, "cores": r["threads"],
+            "sample": f"h-iterated density + force of {r['n_sub']} particles of the Sod tube "
+                      f"shrunk to {scale:g} of its particles ({r['inter']} interactions, "
+                      f"{r['seconds']:.2f} s)"}
 
 
 def run_reference(args, d: Dist):
@@ -451,6 +531,11 @@ def run_ours(args, d: Dist):
                  "interactions_per_step": ointer / args.steps}
         oc.close()
 
+    # config 4: the same boxes as one context each (one launch sequence per box)
+    per_box = None
+    if p.n_boxes > 1 and not args.no_compare:
+        per_box = time_per_box(p, dt, args, dev, stream, flush, tuned, sph, torch)
+
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -490,6 +575,7 @@ def run_ours(args, d: Dist):
                             "D2H x v u h"},
             "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
             "other_form": other,
+            "per_box_launches": per_box,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
