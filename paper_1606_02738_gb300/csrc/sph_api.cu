@@ -86,6 +86,7 @@ struct sph_ctx {
   bool sorts_valid = false;  // pair-axis sorts match the current grid
   bool groups_geom_valid = false;  // group frames and boxes match the current positions
   bool grid_reusable = false;      // the last step's grid passed the reach check
+  int reuse_streak = 0;            // steps run in a row on the current grid
   int regrids_in_step = 0;
   long long grid_stamp = 0;        // bumped by every regrid (sizes, buffers, store swap)
   // steady steps as one CUDA graph (batched FP32 form on a reused grid)
@@ -1319,7 +1320,9 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
     return fail(c, SPH_EINVAL, "dt must be positive and n_steps >= 0");
   for (int s = 0; s < n_steps; ++s) {
     const bool reuse = c->p.reuse_grid && c->grid_reusable && c->grid_valid;
-    const bool graph = reuse && c->p.mode == SPH_MODE_BATCHED && c->groups_valid;
+    // a grid's first reused step runs host-driven; capturing pays from the second on
+    const bool graph =
+        reuse && c->reuse_streak >= 1 && c->p.mode == SPH_MODE_BATCHED && c->groups_valid;
     if (graph)
       TRY(graph_step(c, dt));
     else
@@ -1341,6 +1344,7 @@ int sph_step(sph_ctx *c, double dt, int n_steps) {
     }
     TRY(check_status(c, (c->ctr_h->status | st) & ~kErrHGrid));
     c->grid_reusable = !(st & kErrHGrid);
+    c->reuse_streak = c->regrids_in_step == 0 && reuse ? c->reuse_streak + 1 : 0;
   }
   return sync_check(c);
 }

@@ -41,8 +41,8 @@ def test_sod_steps_on_reused_grid_match_oracle(mode):
     g = _steps(p, n, dt, mode=mode)
     st = g["stats"]
     assert st["reused_steps"] >= n - 2, st["reused_steps"]
-    if mode == sph.SPH_MODE_BATCHED:  # steps on a reused grid run as one CUDA graph
-        assert st["graph_steps"] == st["reused_steps"], st["graph_steps"]
+    if mode == sph.SPH_MODE_BATCHED:  # from a grid's second reused step on: one CUDA graph
+        assert 1 <= st["graph_steps"] <= st["reused_steps"] - 1, st["graph_steps"]
     else:
         assert st["graph_steps"] == 0
     s = run_oracle(p, steps=n, dt=dt)
