@@ -729,16 +729,18 @@ constexpr float kSkinList = 1.05f;   // per-lane list radius = 1.05 x the lane's
 // per-pass loop.
 // The kernels of the batched density (group frames if stale, h maxima, the
 // walk, the three tiers), no host reads.
-int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P) {
+// `hmax_current`: the node and group h maxima still hold for the current h
+// (a steady step: h has not changed since the last force's walk).
+int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P, bool hmax_current = false) {
   if (!c->groups_valid) TRY(build_groups(c));
   if (!c->groups_geom_valid) {  // positions moved on an unchanged grid
     launch_group_geometry(group_args(c), c->stream);
     c->groups_geom_valid = true;
   }
-  GroupBuildArgs ga = group_args(c);
-  launch_group_hmax(ga, c->stream);
-  GeomArgs gg = geom_args(c);
-  launch_leaf_hmax(gg, c->n_nodes, c->stream);
+  if (!hmax_current) {
+    launch_group_hmax(group_args(c), c->stream);
+    launch_leaf_hmax(geom_args(c), c->n_nodes, c->stream);
+  }
   TRY(build_group_lists(c, false, kSkinStage, c->gd_off, c->gd_tasks));
   BatchDensArgs da{};
   da.n_groups = c->n_groups;
@@ -1095,12 +1097,13 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   ga.maxout = c->boxout;
   launch_refresh_geometry(ga, c->n_nodes, c->stream);
   toc(c, kGrid);
-  launch_h_guess(geom_args(c), c->p.n_ngb, c->st.h, c->hf, c->stream);
+  // no starting-guess pass: h is the last step's converged h (the guess only
+  // replaces an h more than 2x away from the leaf-density estimate)
   launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, c->n, c->stream);
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
   launch_group_geometry(group_args(c), c->stream);
   c->groups_geom_valid = true;
-  TRY(enqueue_density_batched(c, c->st.vu_pred));
+  TRY(enqueue_density_batched(c, c->st.vu_pred, true));
   TRY(enqueue_force_batched(c, c->st.vu_pred));
   tic(c, kInteg2);
   launch_kick(c->st, c->n, dt, c->ctr, c->stream);
