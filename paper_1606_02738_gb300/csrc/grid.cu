@@ -622,6 +622,7 @@ constexpr int kWalkStack = 96;
 __global__ void k_lists(ListArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_targets) return;
+  if (!a.flag[t]) return;  // the warp walk handled this target
   const int T = a.active ? a.active[t] : t;
   const Leaf LT = a.leaves[T];
   const Node NT = a.nodes[LT.node];
@@ -678,9 +679,118 @@ __global__ void k_lists(ListArgs a) {
   if (!fill) a.count[t] = cnt;
 }
 
+constexpr int kLWarps = 4;
+constexpr int kLFront = 512;
+
+// One warp per target leaf: the walk of k_lists (the 27 neighbouring top-cell
+// octrees, every leaf whose box lies within reach of the target leaf's box),
+// breadth first, the lanes testing 32 frontier nodes at a time; passing
+// leaves are appended by ballot in walk order. A frontier beyond kLFront
+// marks the target (flag) for k_lists instead.
+__global__ void __launch_bounds__(kLWarps * 32) k_lists_warp(ListArgs a) {
+  __shared__ int2 front_all[kLWarps][2][kLFront];  // (node, neighbour code 0..26)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned ltmask = (1u << lane) - 1u;
+  const int t = blockIdx.x * kLWarps + warp;
+  if (t >= a.n_targets) return;  // warp-uniform
+  const bool fill = a.tasks != nullptr;
+  if (fill && a.flag[t]) return;
+  int2 *cur = front_all[warp][0], *nxt = front_all[warp][1];
+  const int T = a.active ? a.active[t] : t;
+  const Leaf LT = a.leaves[T];
+  const Node NT = a.nodes[LT.node];
+  const BoxDev &B = a.boxes[LT.box];
+  int c[3];
+  cell_coords(B, NT.cell - B.cell_base, c);
+  const float capT = a.force ? NT.hmax : NT.hmax * a.cap_factor;
+  const int base = fill ? a.offset[t] : 0;
+  int n = 0;
+  {
+    const bool in = lane < 27;
+    int2 e = make_int2(0, lane);
+    if (in) {
+      const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+      const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
+                         (c[2] + dz + B.n[2]) % B.n[2]};
+      e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) cur[__popc(m & ltmask)] = e;
+    n = __popc(m);
+  }
+  __syncwarp();
+  int ntask = 0;
+  bool overflow = false;
+  while (n > 0) {
+    int nn = 0;
+    for (int b0 = 0; b0 < n; b0 += 32) {
+      const int idx = b0 + lane;
+      bool leaf_in = false, inner_in = false;
+      int code = 0, child = 0, leaf = 0;
+      if (idx < n) {
+        const int2 e = cur[idx];
+        code = e.y;
+        const Node &S = a.nodes[e.x];
+        if (S.count > 0) {
+          const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+          const float sh[3] = {dx * B.wf[0], dy * B.wf[1], dz * B.wf[2]};
+          float d2 = 0.f;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float g = fmaxf(0.f, fmaxf((S.lo[d] + sh[d]) - NT.hi[d], NT.lo[d] - (S.hi[d] + sh[d])));
+            d2 = fmaf(g, g, d2);
+          }
+          const float crit = (a.force ? fmaxf(capT, S.hmax) : capT) + B.eps;
+          if (d2 < crit * crit) {
+            child = S.child;
+            leaf = S.leaf;
+            leaf_in = child < 0;
+            inner_in = child >= 0;
+          }
+        }
+      }
+      const unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
+      if (leaf_in && fill) {
+        const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
+        const Leaf &LS = a.leaves[leaf];
+        Task tk;
+        tk.sx = (float)(LS.o[0] + dx * B.w[0] - LT.o[0]);
+        tk.sy = (float)(LS.o[1] + dy * B.w[1] - LT.o[1]);
+        tk.sz = (float)(LS.o[2] + dz * B.w[2] - LT.o[2]);
+        tk.src = leaf;
+        a.tasks[base + ntask + __popc(ml & ltmask)] = tk;
+      }
+      ntask += __popc(ml);
+      const unsigned mi = __ballot_sync(0xffffffffu, inner_in);
+      if (inner_in) {
+        const int pos = nn + 8 * __popc(mi & ltmask);
+        for (int o = 0; o < 8; ++o)
+          if (pos + o < kLFront) nxt[pos + o] = make_int2(child + o, code);
+      }
+      nn += 8 * __popc(mi);
+    }
+    __syncwarp();
+    if (nn > kLFront) {
+      overflow = true;
+      break;
+    }
+    int2 *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    n = nn;
+  }
+  if (lane == 0 && !fill) {
+    a.flag[t] = overflow ? 1 : 0;
+    if (!overflow) a.count[t] = ntask;
+  }
+}
+
 void launch_build_lists(const ListArgs &a, cudaStream_t s) {
   if (a.n_targets <= 0) return;
-  k_lists<<<(a.n_targets + 127) / 128, 128, 0, s>>>(a); note_launch();
+  k_lists_warp<<<(a.n_targets + kLWarps - 1) / kLWarps, kLWarps * 32, 0, s>>>(a);
+  note_launch();
+  k_lists<<<(a.n_targets + 127) / 128, 128, 0, s>>>(a);  // flagged targets only
+  note_launch();
 }
 
 }  // namespace sph

@@ -70,7 +70,7 @@ struct sph_ctx {
 
   // growable, library-owned
   // batched form: target groups and their task lists
-  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue;
+  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue, lflag;
   int n_groups = 0;
   bool groups_valid = false;
   int64_t n_gd_tasks = 0, n_gf_tasks = 0;
@@ -597,6 +597,7 @@ GeomArgs geom_args(sph_ctx *c) {
 int build_lists_inner(sph_ctx *c, bool force, const int *active, int n_targets, DevBuf &off,
                       DevBuf &tasks, int64_t &n_tasks) {
   TRY(ensure(c, off, sizeof(int) * (size_t)(n_targets + 1)));
+  TRY(ensure(c, c->lflag, sizeof(int) * (size_t)std::max(n_targets, 1)));
   ListArgs la{};
   la.n_leaves = c->n_leaves;
   la.leaves = as<Leaf>(c->leaves);
@@ -611,6 +612,7 @@ int build_lists_inner(sph_ctx *c, bool force, const int *active, int n_targets, 
   la.active = active;
   la.n_targets = n_targets;
   la.status = &c->ctr->status;
+  la.flag = as<int>(c->lflag);
   CUDA_TRY(cudaMemsetAsync(as<int>(off) + n_targets, 0, sizeof(int), c->stream));
   launch_build_lists(la, c->stream);
   exclusive_scan_int(as<int>(off), as<int>(off), n_targets + 1, c->scan_tmp.p, c->scan_tmp.bytes,
@@ -1507,7 +1509,7 @@ void sph_destroy(sph_ctx *c) {
                     &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
                     &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
-                    &c->gqueue};
+                    &c->gqueue,     &c->lflag};
   for (DevBuf *b : bufs) release(*b);
   for (void *p : c->owned) cudaFree(p);
   if (c->ctr) cudaFree(c->ctr);

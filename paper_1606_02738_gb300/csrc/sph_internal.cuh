@@ -448,7 +448,11 @@ struct ListArgs {
   const int *active;   // optional subset of target leaves (NULL = all)
   int n_targets;
   int *status;         // kErrListOverflow if a walk ran out of stack
+  int *flag;           // [n_targets] 1: the warp walk's frontier overflowed for this target
 };
+// Count pass (a.tasks null) or fill pass: one warp per target leaf, breadth
+// first; the few targets whose frontier overflows are walked by one thread
+// each, depth first (same tasks, another order, the same in both passes).
 void launch_build_lists(const ListArgs &a, cudaStream_t s);
 
 // ---- interact.cu ----
