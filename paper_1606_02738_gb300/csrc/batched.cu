@@ -427,11 +427,18 @@ constexpr int kLaneF = 28;       // force list entries per lane (tile 0)
 // tier hold longer lists: clumped inputs put more particles inside 1.05 h)
 constexpr int dens_lane(int ns) { return ns == kStageD ? kLaneD : 48; }
 constexpr int force_lane(int ns) { return ns == kStageF ? kLaneF : 32; }
+static_assert(kLaneD % 4 == 0 && kLaneF % 4 == 0, "lists are padded to multiples of 4");
+
+// Entry NS of a stage is a sentinel (far away, zero mass, zero A): per-lane
+// lists are padded with it to a multiple of 4 entries, so the sums run in
+// steps of 4 with no bounds test; it never passes r^2 < h^2 and adds an
+// exact zero to the FP32 force sums (the compensated sums skip it).
+constexpr float kFar = 1e18f;
 
 template <int NS>
 struct DensSmem {
   float4 tgt[32];                           // tight stage: target position (group frame), radius
-  float4 stage[NS];                         // position in the group frame, m
+  float4 stage[NS + 1];                     // position in the group frame, m; [NS] sentinel
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][dens_lane(NS) * 32];  // [entry][lane]
   int wcount[kNW];
@@ -440,9 +447,9 @@ struct DensSmem {
 template <int NS>
 struct ForceSmem {
   float4 tgt[32];                           // tight stage: target position (group frame), h
-  float4 sq[NS];                            // position in the group frame, m
-  float2 sf[NS];                            // A (8/pi) h^-4, h^2
-  int sj[NS];                               // particle index (velocity read on use)
+  float4 sq[NS + 1];                        // position in the group frame, m; [NS] sentinel
+  float2 sf[NS + 1];                        // A (8/pi) h^-4, h^2
+  int sj[NS + 1];                           // particle index (velocity read on use)
   unsigned short cand[kNW][force_cand(NS)];
   unsigned short list[kNW][force_lane(NS) * 32];
   int wcount[kNW];
@@ -717,6 +724,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
   int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
+  if (threadIdx.x == 0) S.stage[NS] = make_float4(kFar, kFar, kFar, 0.f);  // read after a barrier
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -806,7 +814,12 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
           }
         }
         need_list = false;
-        if (__any_sync(0xffffffffu, cnt > LANE)) mode = 1;
+        if (__any_sync(0xffffffffu, cnt > LANE)) {
+          mode = 1;
+        } else {  // pad every lane's list with the sentinel to the warp's longest, x4
+          const int tpad = (warp_max_int(cnt) + 3) & ~3;
+          for (int t = cnt; t < tpad; ++t) list[t * 32 + lane] = (unsigned short)NS;
+        }
         __syncwarp();
       }
       // partial sums over this lane's slice at the current h
@@ -814,10 +827,15 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
       const float h2 = fin ? -1.f : hf * hf;
       const float hinv = 1.f / hf;
       DensAcc<KAHAN> acc;
-      if (mode == 0) {
-        const int tmax = warp_max_int(fin ? 0 : cnt);
-        for (int t = 0; t < tmax; ++t)
-          if (t < cnt && !fin) acc.add(S.stage[list[t * 32 + lane]], px, py, pz, h2, hinv);
+      if (mode == 0) {  // finished lanes have h2 < 0: nothing passes
+        const int tmax = (warp_max_int(fin ? 0 : cnt) + 3) & ~3;
+        for (int t = 0; t < tmax; t += 4) {
+          int k[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) k[u] = list[(t + u) * 32 + lane];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc.add(S.stage[k[u]], px, py, pz, h2, hinv);
+        }
         if (!fin) ntest += cnt;
       } else {
         const int nsrc = mode == 1 ? ncand : sr.total;
@@ -899,9 +917,12 @@ struct ForceAcc {
   float ax = 0.f, ay = 0.f, az = 0.f, du = 0.f;
   float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;  // Kahan compensations
   int c = 0;
+  // k == skip (the stage sentinel) adds exact zeros; it is not counted and
+  // the compensated sums leave it out.
   template <class SM>
   __device__ __forceinline__ void add(const SM &S, int k, const float4 *vu, float px,
-                                      float py, float pz, float4 fi, float4 vi, float hi2) {
+                                      float py, float pz, float4 fi, float4 vi, float hi2,
+                                      int skip = -1) {
     const float4 q = S.sq[k];
     const float2 f = S.sf[k];
     const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
@@ -914,7 +935,9 @@ struct ForceAcc {
     const float fac = q.w * (ti + tj) * rinv;
     const float4 vj = vu[S.sj[k]];
     const float dvdx = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+    if (KAHAN && k == skip) return;
     accumulate(fac, dx, dy, dz, q.w * ti * rinv * dvdx);
+    if (!KAHAN && k == skip) --c;
   }
   // a -= fac (x_i - x_j), du/dt += the energy term
   __device__ __forceinline__ void accumulate(float fac, float dx, float dy, float dz, float dui) {
@@ -1290,6 +1313,11 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
   int stage_max = 0, n_direct[2] = {0, 0};
+  if (threadIdx.x == 0) {  // read after a barrier
+    S.sq[NS] = make_float4(kFar, kFar, kFar, 0.f);
+    S.sf[NS] = make_float2(0.f, 1.f);
+    S.sj[NS] = 0;
+  }
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -1358,14 +1386,24 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
         }
       }
       if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
-      if (__any_sync(0xffffffffu, cnt > LANE)) mode = 1;
+      if (__any_sync(0xffffffffu, cnt > LANE)) {
+        mode = 1;
+      } else {  // pad every lane's list with the sentinel to the warp's longest, x4
+        const int tpad = (warp_max_int(cnt) + 3) & ~3;
+        for (int t = cnt; t < tpad; ++t) list[t * 32 + lane] = (unsigned short)NS;
+      }
       __syncwarp();
     }
     ForceAcc<KAHAN> acc;
     if (mode == 0) {
-      const int tmax = warp_max_int(has ? cnt : 0);
-      for (int t = 0; t < tmax; ++t)
-        if (t < cnt) acc.add(S, list[t * 32 + lane], a.vu, px, py, pz, fi, vi, -1.f);
+      const int tmax = (warp_max_int(has ? cnt : 0) + 3) & ~3;
+      for (int t = 0; t < tmax; t += 4) {
+        int k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = list[(t + u) * 32 + lane];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc.add(S, k[u], a.vu, px, py, pz, fi, vi, -1.f, NS);
+      }
       if (has) ntest += cnt;
     } else {
       const int nsrc = mode == 1 ? ncand : sr.total;
