@@ -449,6 +449,13 @@ def run_ours(args, d: Dist):
             "kernel": dom, "peak_source": peak_src,
             "flops_per_interaction": {"density": FLOPS_DENSITY, "force": FLOPS_FORCE},
             "kernels": kern}
+    # the second denominator: the FFMA rate this GPU sustains, measured now
+    # (after the timed region, so it does not heat the timed steps)
+    ffma = sph.sph_fp32_peak(dev.index if dev.index is not None else 0)
+    roof["peak_ffma_measured"] = {"value": ffma["tflops"], "unit": "TFLOP/s",
+                                  "frac": kern[dom]["achieved"] / ffma["tflops"],
+                                  "how": "sph_fp32_peak: independent FFMA chains, full "
+                                         "occupancy, best of 5 launches"}
     # the pair-axis sort kernel: HBM-bound, algorithmic bytes per particle =
     # one float4 read + 13 (key, index) pairs written
     t_sort = s1["t_sort_ms"] - s0["t_sort_ms"]

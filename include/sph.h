@@ -137,10 +137,13 @@ typedef struct {
   double t_force_ms;          /* force interaction kernel only */
   double t_integrate_ms;      /* kick / drift kernels */
   double t_sort_ms;           /* pair-axis sorts of every leaf (pair_sort = 1) */
-  /* Last sph_density + sph_force, batched form: warps of a group whose
-   * per-lane neighbour lists overflowed and that read their pre-filtered
-   * candidates directly, and warps whose candidates overflowed and that read
-   * the group's whole stage (same results, more pairs tested). */
+  /* Last sph_density + sph_force, batched form (same results either way):
+   * direct_list_warps = density warps whose per-lane neighbour lists
+   * overflowed and that read their pre-filtered candidates directly, plus
+   * force warps that built their lists in more than one round;
+   * direct_stage_warps = density warps whose candidates overflowed and that
+   * read the group's whole stage, plus force warps that filtered the stage in
+   * more than one chunk. */
   int32_t direct_list_warps;
   int32_t direct_stage_warps;
   /* Particles of the last sph_density + sph_force that the batched kernels
@@ -242,6 +245,17 @@ int sph_autotune(sph_ctx *ctx, int *tile_out, int *n_split_out, double *cell_fac
  * Errors: SPH_EINVAL (axis out of range, null output), SPH_ESTATE (no
  * particles loaded, or pair_sort = 0). */
 int sph_get_pair_order(sph_ctx *ctx, int axis, int32_t *order_out, int32_t *leaf_out);
+
+/* FP32 fused multiply-add rate of `device`, measured (no counterpart in the
+ * paper; the second denominator of the interaction kernels' FP32 roofline,
+ * beside SM count x 128 lanes x 2 flops x the maximum SM clock). Runs
+ * independent FFMA chains at full occupancy on a private stream, best of 5
+ * timed launches (~1 ms each) after a warm-up; an FFMA counts as 2 flops.
+ * Writes TFLOP/s to *tflops_out and the best launch time (ms) to *ms_out
+ * (host pointers; ms_out may be NULL). The calling thread's current device is
+ * restored. Synchronises that device's work on its own stream only.
+ * Errors: SPH_EINVAL (null tflops_out, bad device), SPH_ENOMEM, SPH_ECUDA. */
+int sph_fp32_peak(int device, double *tflops_out, double *ms_out);
 
 /* Counters of the last density/force calls (synchronises the stream). */
 int sph_stats(sph_ctx *ctx, sph_stats_t *out);

@@ -29,19 +29,6 @@ namespace sph {
 namespace {
 
 constexpr int kGroup = 32;
-constexpr int kWalkStack = 96;
-
-__device__ __forceinline__ int box_of_cell_b(const BoxDev *b, int nb, int c) {
-  int lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (b[mid].cell_base <= c)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ void cell_xyz(const BoxDev &B, int local, int c[3]) {
   c[2] = local % B.n[2];
@@ -663,6 +650,37 @@ __device__ __forceinline__ int filter_stage(const float4 *sq, const float2 *sf,
     const unsigned m = __ballot_sync(0xffffffffu, in);
     const int pos = n + __popc(m & ltmask);
     if (in && pos < cap) cand[pos] = (unsigned short)k;
+    n += __popc(m);
+  }
+  __syncwarp();
+  return n;
+}
+
+// The force kernel's filter in chunks: from stage entry `sp` on, entries
+// within max(Rsub, h_j) of the sub-cluster box, compacted in stage order into
+// `cand`, 32 entries at a time while at least 32 slots remain free. Returns
+// the count (<= cap) and advances sp past the entries it examined.
+__device__ __forceinline__ int filter_chunk(const float4 *sq, const float2 *sf,
+                                            const StageRange &sr, int &sp, const float lo[3],
+                                            const float hi[3], float Rsub,
+                                            unsigned short *cand, int cap, int lane) {
+  const unsigned ltmask = (1u << lane) - 1u;
+  int n = 0;
+  for (; sp < sr.total && n <= cap - 32; sp += 32) {
+    const int t = sp + lane;
+    bool in = false;
+    int k = 0;
+    if (t < sr.total) {
+      k = sr.index(t);
+      const float4 q = sq[k];
+      const float R = fmaxf(Rsub, sqrtf(sf[k].y));
+      const float gx = fmaxf(0.f, fmaxf(lo[0] - q.x, q.x - hi[0]));
+      const float gy = fmaxf(0.f, fmaxf(lo[1] - q.y, q.y - hi[1]));
+      const float gz = fmaxf(0.f, fmaxf(lo[2] - q.z, q.z - hi[2]));
+      in = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < R * R;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) cand[n + __popc(m & ltmask)] = (unsigned short)k;
     n += __popc(m);
   }
   __syncwarp();
@@ -1365,55 +1383,82 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     sub_box(has, px, py, pz, blo, bhi);
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-    const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, CANDF, lane);
-    // 0: per-lane lists; 1: a list outgrew LANE, the warp reads its
-    // candidates directly; 2: the candidates outgrew kCandF, it reads the
-    // whole stage (ncand is warp-uniform)
-    int mode = ncand > CANDF ? 2 : 0;
     const float hi2 = has ? fi.w : -1.f;
-    int cnt = 0;
-    if (mode == 0) {
-#pragma unroll 4
-      for (int t = slice; t < ncand; t += kSlice) {
-        const int k = cand[t];
-        const float4 q = S.sq[k];
-        const float hj2 = S.sf[k].y;
-        const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-          if (cnt < LANE) list[cnt * 32 + lane] = (unsigned short)k;
-          ++cnt;
-        }
-      }
-      if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
-      if (__any_sync(0xffffffffu, cnt > LANE)) {
-        mode = 1;
-      } else {  // pad every lane's list with the sentinel to the warp's longest, x4
-        const int tpad = (warp_max_int(cnt) + 3) & ~3;
-        for (int t = cnt; t < tpad; ++t) list[t * 32 + lane] = (unsigned short)NS;
-      }
-      __syncwarp();
-    }
+    // The stage is filtered in chunks of at most CANDF candidates, and each
+    // chunk's per-lane lists are built and summed in rounds of at most LANE
+    // entries per lane (a lane resumes its scan where the last round
+    // stopped). The common case is one chunk and one round; every case sums
+    // the same pairs in the same per-lane order.
     ForceAcc<KAHAN> acc;
-    if (mode == 0) {
-      const int tmax = (warp_max_int(has ? cnt : 0) + 3) & ~3;
-      for (int t = 0; t < tmax; t += 4) {
-        int k[4];
+    int sp = 0, chunks = 0, rounds = 0;  // sp: next stage entry to filter (warp-uniform)
+    while (sp < sr.total) {
+      const int ncand = filter_chunk(S.sq, S.sf, sr, sp, blo, bhi, hm, cand, CANDF, lane);
+      ++chunks;
+      int tpos = has ? slice : ncand;  // this lane's next candidate
+      bool first = true;
+      do {
+        const int t0 = tpos;
+        int cnt = 0;
+        if (first) {  // scan every candidate; note where the list filled up
+          int tres = ncand;
+#pragma unroll 4
+          for (; tpos < ncand; tpos += kSlice) {
+            const int k = cand[tpos];
+            const float4 q = S.sq[k];
+            const float hj2 = S.sf[k].y;
+            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+              if (cnt < LANE)
+                list[cnt * 32 + lane] = (unsigned short)k;
+              else if (cnt == LANE)
+                tres = tpos;  // the first neighbour left out: the next round starts here
+              ++cnt;
+            }
+          }
+          if (cnt > LANE) {
+            cnt = LANE;
+            tpos = tres;
+          }
+          first = false;
+        } else {  // later rounds stop as soon as the list is full
+#pragma unroll 4
+          for (; tpos < ncand; tpos += kSlice) {
+            const int k = cand[tpos];
+            const float4 q = S.sq[k];
+            const float hj2 = S.sf[k].y;
+            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+              list[cnt * 32 + lane] = (unsigned short)k;
+              if (++cnt == LANE) {
+                tpos += kSlice;
+                break;
+              }
+            }
+          }
+        }
+        ntest += (max(tpos, t0) - t0) / kSlice + cnt;
+        // pad every lane's list with the sentinel to the warp's longest, x4
+        const int tmax = (warp_max_int(cnt) + 3) & ~3;
+        for (int t = cnt; t < tmax; ++t) list[t * 32 + lane] = (unsigned short)NS;
+        __syncwarp();
+        for (int t = 0; t < tmax; t += 4) {
+          int k[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = list[(t + u) * 32 + lane];
+          for (int u = 0; u < 4; ++u) k[u] = list[(t + u) * 32 + lane];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc.add(S, k[u], a.vu, px, py, pz, fi, vi, -1.f, NS);
-      }
-      if (has) ntest += cnt;
-    } else {
-      const int nsrc = mode == 1 ? ncand : sr.total;
-      if (has)
-        for (int t = slice; t < nsrc; t += kSlice)
-          acc.add(S, mode == 1 ? (int)cand[t] : sr.index(t), a.vu, px, py, pz, fi, vi, hi2);
-      if (has) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
+          for (int u = 0; u < 4; ++u) acc.add(S, k[u], a.vu, px, py, pz, fi, vi, -1.f, NS);
+        }
+        ++rounds;
+        __syncwarp();  // the next round rewrites the lists
+      } while (__any_sync(0xffffffffu, tpos < ncand));
     }
-    if (lane == 0 && mode) ++n_direct[mode - 1];
-    cnt = acc.c;
+    if (lane == 0) {
+      n_direct[0] += rounds > chunks;
+      n_direct[1] += chunks > 1;
+    }
+    int cnt = acc.c;
     float ax = acc.ax, ay = acc.ay, az = acc.az, du = acc.du;
     ax = slice_sum(ax);
     ay = slice_sum(ay);

@@ -89,7 +89,7 @@ def header_functions() -> list[str]:
     """Names of the functions declared in include/sph.h."""
     hdr = os.path.join(_build.ROOT, "include", "sph.h")
     text = open(hdr).read()
-    return sorted(set(re.findall(r"\b(sph_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", text)))
 
 
 def lib(build_if_needed: bool = True):
@@ -115,6 +115,7 @@ def lib(build_if_needed: bool = True):
         L.sph_get.argtypes = [P, I, P]
         L.sph_get_pair_order.argtypes = [P, I, P, P]
         L.sph_autotune.argtypes = [P, P, P, P, P]
+        L.sph_fp32_peak.argtypes = [I, P, P]
         L.sph_stats.argtypes = [P, ctypes.POINTER(sph_stats_t)]
         L.sph_last_error.argtypes = [P]
         L.sph_last_error.restype = ctypes.c_char_p
@@ -122,7 +123,7 @@ def lib(build_if_needed: bool = True):
         L.sph_destroy.restype = None
         for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
                   "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
-                  "sph_autotune", "sph_stats"):
+                  "sph_autotune", "sph_fp32_peak", "sph_stats"):
             getattr(L, f).restype = I
         _lib = L
         return L
@@ -227,6 +228,14 @@ def sph_autotune(ctx) -> dict:
                                    ctypes.byref(ms)), "sph_autotune")
     return {"tile": tile.value, "n_split": ns.value, "cell_factor": cf.value,
             "best_ms": ms.value}
+
+
+def sph_fp32_peak(device: int = 0) -> dict:
+    """Measured FP32 FFMA rate of a device (TFLOP/s) and the best launch time."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().sph_fp32_peak(int(device), ctypes.byref(tf), ctypes.byref(ms)),
+           "sph_fp32_peak")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def sph_stats(ctx) -> dict:

@@ -20,7 +20,8 @@ def test_header_declares_the_boundary():
     names = sph.header_functions()
     for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
               "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
-              "sph_autotune", "sph_stats", "sph_last_error", "sph_destroy", "sph_default_params"):
+              "sph_autotune", "sph_fp32_peak", "sph_stats", "sph_last_error", "sph_destroy",
+              "sph_default_params"):
         assert f in names
 
 
@@ -70,4 +71,5 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     assert L.sph_create(ctypes.byref(ctx), ctypes.byref(bad), None) == sph.SPH_EINVAL
     assert L.sph_density(None) == sph.SPH_EINVAL
     assert L.sph_stats(None, None) == sph.SPH_EINVAL
+    assert L.sph_fp32_peak(0, None, None) == sph.SPH_EINVAL
     L.sph_destroy(None)
