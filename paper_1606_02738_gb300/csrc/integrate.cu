@@ -106,14 +106,26 @@ void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *o
   k_permute<<<(n + 255) / 256, 256, 0, s>>>(dst, src, order, n); note_launch();
 }
 
-// First half kick, drift, prediction.
+// First half kick, drift, prediction of v and u, and the starting guess of
+// the next h iteration: with a constant neighbour number h varies as
+// rho^(-1/3), and in the adiabatic flow d ln rho / dt = (du/dt) / ((gamma-1) u)
+// (the same velocity-divergence sum as du/dt), so h is carried to the end of
+// the step as h exp(-dt (du/dt) / (3 (gamma-1) u)). Only the guess moves: the
+// density stage still iterates h to its own root (Section 2, constant
+// neighbour number), so results do not depend on it beyond the tolerance.
 __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int nb,
-                             DevCounters *ctr) {
+                             float gm1, float *hf, DevCounters *ctr) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float hdt = (float)(0.5 * dt);
   const float4 a = st.acc[s];
   float4 v = st.vu[s];
+  if (v.w > 0.f && a.w != 0.f) {
+    const float e = fminf(fmaxf(-(float)dt * a.w / (3.f * gm1 * v.w), -0.2f), 0.2f);
+    const double h = st.h[s] * (double)expf(e);
+    st.h[s] = h;
+    hf[s] = (float)h;
+  }
   v.x = fmaf(a.x, hdt, v.x);
   v.y = fmaf(a.y, hdt, v.y);
   v.z = fmaf(a.z, hdt, v.z);
@@ -130,8 +142,10 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
 }
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
-                       DevCounters *ctr, cudaStream_t s) {
-  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, ctr); note_launch();
+                       double gamma, float *hf, DevCounters *ctr, cudaStream_t s) {
+  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, (float)(gamma - 1.0),
+                                                 hf, ctr);
+  note_launch();
 }
 
 // Closing half kick with the new accelerations.

@@ -1065,7 +1065,7 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
   if (reuse) copy_step_state(c, c->st, c->st2);
   tic(c, kInteg);
-  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, c->ctr, c->stream);
   toc(c, kInteg);
   c->density_valid = false;
   c->force_valid = false;
@@ -1091,7 +1091,7 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
   copy_step_state(c, c->st, c->st2);
   tic(c, kInteg);
-  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->ctr, c->stream);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, c->ctr, c->stream);
   toc(c, kInteg);
   tic(c, kGrid);
   CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
@@ -1099,8 +1099,11 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   ga.maxout = c->boxout;
   launch_refresh_geometry(ga, c->n_nodes, c->stream);
   toc(c, kGrid);
-  // no starting-guess pass: h is the last step's converged h (the guess only
-  // replaces an h more than 2x away from the leaf-density estimate)
+  // no starting-guess pass: h is the last step's converged h carried by the
+  // drift (the guess only replaces an h more than 2x away from the
+  // leaf-density estimate); the h maxima of the last force still bound it to
+  // within the stage skin, and a target whose h leaves its staged radius is
+  // finished by the third tier
   launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, c->n, c->stream);
   CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
   launch_group_geometry(group_args(c), c->stream);
