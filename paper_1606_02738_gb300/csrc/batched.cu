@@ -1384,65 +1384,39 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     float hm = has ? fi.x : 0.f;
     for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
     const float hi2 = has ? fi.w : -1.f;
-    // The stage is filtered in chunks of at most CANDF candidates, and each
-    // chunk's per-lane lists are built and summed in rounds of at most LANE
-    // entries per lane (a lane resumes its scan where the last round
-    // stopped). The common case is one chunk and one round; every case sums
-    // the same pairs in the same per-lane order.
     ForceAcc<KAHAN> acc;
-    int sp = 0, chunks = 0, rounds = 0;  // sp: next stage entry to filter (warp-uniform)
-    while (sp < sr.total) {
-      const int ncand = filter_chunk(S.sq, S.sf, sr, sp, blo, bhi, hm, cand, CANDF, lane);
-      ++chunks;
-      int tpos = has ? slice : ncand;  // this lane's next candidate
-      bool first = true;
-      do {
-        const int t0 = tpos;
-        int cnt = 0;
-        if (first) {  // scan every candidate; note where the list filled up
-          int tres = ncand;
+    if constexpr (NS == kStageF) {
+      // tile 0 (inputs without strong clumps): one filter of the stage into
+      // cand, one list per lane; a warp whose list outgrows LANE reads its
+      // candidates directly, one whose candidates outgrow CANDF reads the
+      // whole stage (rare here; the lean loop keeps this tile's registers)
+      const int ncand = filter_stage<true>(S.sq, S.sf, sr, blo, bhi, hm, cand, CANDF, lane);
+      int mode = ncand > CANDF ? 2 : 0;  // ncand is warp-uniform
+      int cnt = 0;
+      if (mode == 0) {
 #pragma unroll 4
-          for (; tpos < ncand; tpos += kSlice) {
-            const int k = cand[tpos];
-            const float4 q = S.sq[k];
-            const float hj2 = S.sf[k].y;
-            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-              if (cnt < LANE)
-                list[cnt * 32 + lane] = (unsigned short)k;
-              else if (cnt == LANE)
-                tres = tpos;  // the first neighbour left out: the next round starts here
-              ++cnt;
-            }
-          }
-          if (cnt > LANE) {
-            cnt = LANE;
-            tpos = tres;
-          }
-          first = false;
-        } else {  // later rounds stop as soon as the list is full
-#pragma unroll 4
-          for (; tpos < ncand; tpos += kSlice) {
-            const int k = cand[tpos];
-            const float4 q = S.sq[k];
-            const float hj2 = S.sf[k].y;
-            const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
-              list[cnt * 32 + lane] = (unsigned short)k;
-              if (++cnt == LANE) {
-                tpos += kSlice;
-                break;
-              }
-            }
+        for (int t = slice; t < ncand; t += kSlice) {
+          const int k = cand[t];
+          const float4 q = S.sq[k];
+          const float hj2 = S.sf[k].y;
+          const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (has && r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+            if (cnt < LANE) list[cnt * 32 + lane] = (unsigned short)k;
+            ++cnt;
           }
         }
-        ntest += (max(tpos, t0) - t0) / kSlice + cnt;
-        // pad every lane's list with the sentinel to the warp's longest, x4
-        const int tmax = (warp_max_int(cnt) + 3) & ~3;
-        for (int t = cnt; t < tmax; ++t) list[t * 32 + lane] = (unsigned short)NS;
+        if (has) ntest += (ncand + kSlice - 1 - slice) / kSlice;
+        if (__any_sync(0xffffffffu, cnt > LANE)) {
+          mode = 1;
+        } else {  // pad every lane's list with the sentinel to the warp's longest, x4
+          const int tpad = (warp_max_int(cnt) + 3) & ~3;
+          for (int t = cnt; t < tpad; ++t) list[t * 32 + lane] = (unsigned short)NS;
+        }
         __syncwarp();
+      }
+      if (mode == 0) {
+        const int tmax = (warp_max_int(has ? cnt : 0) + 3) & ~3;
         for (int t = 0; t < tmax; t += 4) {
           int k[4];
 #pragma unroll
@@ -1450,13 +1424,90 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
 #pragma unroll
           for (int u = 0; u < 4; ++u) acc.add(S, k[u], a.vu, px, py, pz, fi, vi, -1.f, NS);
         }
-        ++rounds;
-        __syncwarp();  // the next round rewrites the lists
-      } while (__any_sync(0xffffffffu, tpos < ncand));
-    }
-    if (lane == 0) {
-      n_direct[0] += rounds > chunks;
-      n_direct[1] += chunks > 1;
+        if (has) ntest += cnt;
+      } else {
+        const int nsrc = mode == 1 ? ncand : sr.total;
+        if (has)
+          for (int t = slice; t < nsrc; t += kSlice)
+            acc.add(S, mode == 1 ? (int)cand[t] : sr.index(t), a.vu, px, py, pz, fi, vi, hi2);
+        if (has) ntest += (nsrc + kSlice - 1 - slice) / kSlice;
+      }
+      if (lane == 0 && mode) ++n_direct[mode - 1];
+    } else {
+      // tile 1 and the second tier (clumped inputs): the stage is filtered
+      // in chunks of at most CANDF candidates, and each chunk's per-lane
+      // lists are built and summed in rounds of at most LANE entries per
+      // lane (a lane resumes its scan where its last round stopped). The
+      // common case is one chunk and one round; every case sums the same
+      // pairs in the same per-lane order.
+      int sp = 0, chunks = 0, rounds = 0;  // sp: next stage entry to filter (warp-uniform)
+      while (sp < sr.total) {
+        const int ncand = filter_chunk(S.sq, S.sf, sr, sp, blo, bhi, hm, cand, CANDF, lane);
+        ++chunks;
+        int tpos = has ? slice : ncand;  // this lane's next candidate
+        bool first = true;
+        do {
+          const int t0 = tpos;
+          int cnt = 0;
+          if (first) {  // scan every candidate; note where the list filled up
+            int tres = ncand;
+  #pragma unroll 4
+            for (; tpos < ncand; tpos += kSlice) {
+              const int k = cand[tpos];
+              const float4 q = S.sq[k];
+              const float hj2 = S.sf[k].y;
+              const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+                if (cnt < LANE)
+                  list[cnt * 32 + lane] = (unsigned short)k;
+                else if (cnt == LANE)
+                  tres = tpos;  // the first neighbour left out: the next round starts here
+                ++cnt;
+              }
+            }
+            if (cnt > LANE) {
+              cnt = LANE;
+              tpos = tres;
+            }
+            first = false;
+          } else {  // later rounds stop as soon as the list is full
+  #pragma unroll 4
+            for (; tpos < ncand; tpos += kSlice) {
+              const int k = cand[tpos];
+              const float4 q = S.sq[k];
+              const float hj2 = S.sf[k].y;
+              const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              if (r2 > 0.f && r2 < fmaxf(hi2, hj2)) {
+                list[cnt * 32 + lane] = (unsigned short)k;
+                if (++cnt == LANE) {
+                  tpos += kSlice;
+                  break;
+                }
+              }
+            }
+          }
+          ntest += (max(tpos, t0) - t0) / kSlice + cnt;
+          // pad every lane's list with the sentinel to the warp's longest, x4
+          const int tmax = (warp_max_int(cnt) + 3) & ~3;
+          for (int t = cnt; t < tmax; ++t) list[t * 32 + lane] = (unsigned short)NS;
+          __syncwarp();
+          for (int t = 0; t < tmax; t += 4) {
+            int k[4];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = list[(t + u) * 32 + lane];
+  #pragma unroll
+            for (int u = 0; u < 4; ++u) acc.add(S, k[u], a.vu, px, py, pz, fi, vi, -1.f, NS);
+          }
+          ++rounds;
+          __syncwarp();  // the next round rewrites the lists
+        } while (__any_sync(0xffffffffu, tpos < ncand));
+      }
+      if (lane == 0) {
+        n_direct[0] += rounds > chunks;
+        n_direct[1] += chunks > 1;
+      }
     }
     int cnt = acc.c;
     float ax = acc.ax, ay = acc.ay, az = acc.az, du = acc.du;

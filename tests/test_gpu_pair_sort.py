@@ -142,16 +142,19 @@ def test_pruned_per_pass_form_matches_unpruned_and_oracle(make):
     assert s1["force_pair_candidates"] < s0["force_pair_candidates"]
 
 
-def test_batched_direct_modes_match_oracle():
+@pytest.mark.parametrize("tile", [0, 1])
+def test_batched_direct_modes_match_oracle(tile):
     """Large neighbour numbers overflow the batched kernels' per-lane lists
     (n_ngb >= 120) and the force kernel's per-warp candidate lists (around
-    n_ngb = 160-200, while its stage still fits): those warps read their
-    candidates, or the whole stage, directly and must give the same results."""
+    n_ngb = 160-200, while its stage still fits). With tile 0 those warps read
+    their candidates, or the whole stage, directly; with tile 1 the density
+    does the same and the force works through its candidates in chunks and
+    its lists in rounds. Every form must give the oracle's results."""
     direct = np.zeros(2, dtype=np.int64)
     for n_ngb in (120.0, 160.0, 200.0):
         p = inputs.uniform(12000, seed=321, sigma_v=0.2)
         p.n_ngb = n_ngb
-        g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, n_ngb=n_ngb)
+        g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, n_ngb=n_ngb, tile=tile)
         s = run_oracle(p)
         compare_density(g, s)
         compare_force(g, s)

@@ -28,12 +28,13 @@ def _cuda():
     sph.lib()
 
 
-@pytest.mark.parametrize("precision", [sph.SPH_PREC_FP32, sph.SPH_PREC_KAHAN])
-def test_clustered_from_flat_guess_uses_tiers_2_and_3(precision):
+@pytest.mark.parametrize("precision,tile", [(sph.SPH_PREC_FP32, 0), (sph.SPH_PREC_KAHAN, 0),
+                                            (sph.SPH_PREC_KAHAN, 1)])
+def test_clustered_from_flat_guess_uses_tiers_2_and_3(precision, tile):
     """A uniform initial h over strong clumps: the first density pushes many
     groups past their stage (their h shrinks or grows far from the guess)."""
     p = inputs.clustered(60000, n_spheres=8, seed=11, sigma_v=0.1)
-    g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, precision=precision)
+    g = run_gpu(p, mode=sph.SPH_MODE_BATCHED, precision=precision, tile=tile)
     s = run_oracle(p)
     assert s.h.max() / s.h.min() > 20
     st = g["stats"]
