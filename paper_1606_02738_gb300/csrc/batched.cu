@@ -228,14 +228,16 @@ void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s) {
 constexpr int kWalkWarps = 4;
 constexpr int kFront = 512;
 
-__global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a, int tight) {
-  __shared__ int2 front_all[kWalkWarps][2][kFront];  // (node, neighbour code 0..26)
+template <bool TIGHT>
+__global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(GroupListArgs a) {
+  __shared__ int front_all[kWalkWarps][2][kFront];  // node << 5 | neighbour code (0..26)
+  constexpr bool tight = TIGHT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ltmask = (1u << lane) - 1u;
   const int ng = tight ? *a.walk_queued : a.n_groups;
   for (int q = blockIdx.x * kWalkWarps + warp; q < ng; q += gridDim.x * kWalkWarps) {
     const int g = tight ? a.walk_queue[q] : q;
-    int2 *cur = front_all[warp][0], *nxt = front_all[warp][1];
+    int *cur = front_all[warp][0], *nxt = front_all[warp][1];
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     int c[3];
@@ -260,12 +262,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
     int n = 0;
     {
       bool in = lane < 27;
-      int2 e = make_int2(0, lane);
+      int e = lane;
       if (in) {
         const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
         const int nc[3] = {(c[0] + dx + B.n[0]) % B.n[0], (c[1] + dy + B.n[1]) % B.n[1],
                            (c[2] + dz + B.n[2]) % B.n[2]};
-        e.x = B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2];
+        e |= (B.cell_base + (nc[0] * B.n[1] + nc[1]) * B.n[2] + nc[2]) << 5;
       }
       const unsigned m = __ballot_sync(0xffffffffu, in);
       if (in) cur[__popc(m & ltmask)] = e;
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
         int code = 0, child = 0, leaf = 0;
         float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f}, shm = 0.f;
         if (idx < n) {
-          const int2 e = cur[idx];
-          code = e.y;
-          const Node &S = a.nodes[e.x];
+          const int e = cur[idx];
+          code = e & 31;
+          const Node &S = a.nodes[e >> 5];
           if (S.count > 0) {
             const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
             const float sh[3] = {dx * B.wf[0], dy * B.wf[1], dz * B.wf[2]};
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
         if (inner_in) {
           const int pos = nn + 8 * __popc(mi & ltmask);
           for (int o = 0; o < 8; ++o)
-            if (pos + o < kFront) nxt[pos + o] = make_int2(child + o, code);
+            if (pos + o < kFront) nxt[pos + o] = ((child + o) << 5) | code;
         }
         nn += 8 * __popc(mi);
       }
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
         overflow = true;
         break;
       }
-      int2 *t = cur;
+      int *t = cur;
       cur = nxt;
       nxt = t;
       n = nn;
@@ -371,12 +373,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_group_walk(GroupListArgs a,
 // device).
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  k_group_walk<<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a, 0);
+  k_group_walk<false><<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a);
   note_launch();
   if (!a.walk_queue) return;
   const int blocks = a.n_groups < 152 * 8 * kWalkWarps ? (a.n_groups + kWalkWarps - 1) / kWalkWarps
                                                        : 152 * 8;
-  k_group_walk<<<blocks, kWalkWarps * 32, 0, s>>>(a, 1);
+  k_group_walk<true><<<blocks, kWalkWarps * 32, 0, s>>>(a);
   note_launch();
 }
 

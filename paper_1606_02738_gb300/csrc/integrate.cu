@@ -32,6 +32,20 @@ __device__ __forceinline__ double wrap1(double x, double L) {
   return y;
 }
 
+// The drift of one step moves a particle by much less than a box length: one
+// conditional add brings it back, and only a coordinate still outside [0, L)
+// pays for the general form's FP64 division (FP64 runs at 1/64 of the FP32
+// rate here).
+__device__ __forceinline__ double wrap_near(double x, double L) {
+  double y = x;
+  if (y >= L)
+    y -= L;
+  else if (y < 0.0)
+    y += L;
+  if (y >= L || y < 0.0) y = wrap1(x, L);
+  return y;
+}
+
 // caller x [N][3] -> wrapped SoA copy (caller order)
 __global__ void k_wrap_from_caller(const double *x, const BoxDev *boxes, int nb, int n,
                                    double *x0, double *x1, double *x2) {
@@ -132,9 +146,9 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
   v.w = fmaf(a.w, hdt, v.w);
   st.vu[s] = v;  // v and u at the half step
   const BoxDev &B = boxes[box_of_slot(boxes, nb, s)];
-  st.x0[s] = wrap1(st.x0[s] + (double)v.x * dt, B.L[0]);
-  st.x1[s] = wrap1(st.x1[s] + (double)v.y * dt, B.L[1]);
-  st.x2[s] = wrap1(st.x2[s] + (double)v.z * dt, B.L[2]);
+  st.x0[s] = wrap_near(st.x0[s] + (double)v.x * dt, B.L[0]);
+  st.x1[s] = wrap_near(st.x1[s] + (double)v.y * dt, B.L[1]);
+  st.x2[s] = wrap_near(st.x2[s] + (double)v.z * dt, B.L[2]);
   const float4 p = make_float4(fmaf(a.x, hdt, v.x), fmaf(a.y, hdt, v.y), fmaf(a.z, hdt, v.z),
                                fmaf(a.w, hdt, v.w));
   st.vu_pred[s] = p;

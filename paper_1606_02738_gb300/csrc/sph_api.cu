@@ -696,6 +696,9 @@ constexpr int kTaskCap = 384;  // task slots per group
 // round trip).
 int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &tasks) {
   const Stage stage = force ? kLists2 : kLists;
+  if (c->n_nodes >= kWalkMaxNodes)
+    return fail(c, SPH_ENOMEM, "octree of %d nodes exceeds the walk's node index (2^26)",
+                c->n_nodes);
   tic(c, stage);
   const int ng = c->n_groups;
   TRY(ensure(c, cnt, sizeof(int) * (size_t)std::max(ng, 1)));

@@ -565,6 +565,8 @@ struct GroupListArgs {
   int *walk_queue;       // [n_groups] groups whose walk overflowed (null: no tight walk)
   int *walk_queued;      // device count of walk_queue, zero on entry
 };
+// The walk packs (node, neighbour code) into one int: node indices below 2^26.
+constexpr int kWalkMaxNodes = 1 << 26;
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
 
 struct BatchDensArgs {
