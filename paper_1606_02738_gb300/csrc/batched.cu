@@ -153,19 +153,24 @@ __global__ void k_group_geometry(GroupBuildArgs a) {
   if (g >= a.n_groups) return;
   Group *G = &a.groups[g];
   const int start = G->start, count = G->count;
-  const Leaf &L0 = a.leaves[a.leaf_of[start]];
+  const int leaf0 = a.leaf_of[start];
+  const Leaf &L0 = a.leaves[leaf0];
   const double o[3] = {L0.o[0], L0.o[1], L0.o[2]};
   float flo[3] = {3e38f, 3e38f, 3e38f}, fhi[3] = {-3e38f, -3e38f, -3e38f};
   float tlo[3] = {3e38f, 3e38f, 3e38f}, thi[3] = {-3e38f, -3e38f, -3e38f};
   if (lane < count) {
     const int i = start + lane;
-    const Leaf &L = a.leaves[a.leaf_of[i]];
+    const int li = a.leaf_of[i];
+    const Leaf &L = a.leaves[li];
     const float4 q = a.pm[i];
     const float pq[3] = {q.x, q.y, q.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const float f = pq[d] + (float)(L.o[d] - o[d]);
-      const float t = (float)(L.o[d] + (double)pq[d]);
+      // group frame: the leaf offset from the group's first leaf, formed in
+      // FP64 and rounded once; top-cell frame (the walk's box, which has a
+      // pruning margin) in FP32
+      const float f = li == leaf0 ? pq[d] : pq[d] + (float)(L.o[d] - o[d]);
+      const float t = L.of[d] + pq[d];
       flo[d] = fhi[d] = f;
       tlo[d] = thi[d] = t;
     }

@@ -371,6 +371,8 @@ __global__ void k_fill_leaves(Node *nodes, int n_nodes, const int *excl, Leaf *l
   L.o[0] = (double)nd.ix * (B.w[0] * scale);
   L.o[1] = (double)nd.iy * (B.w[1] * scale);
   L.o[2] = (double)nd.iz * (B.w[2] * scale);
+  for (int d = 0; d < 3; ++d) L.of[d] = (float)L.o[d];
+  L.pad = 0;
   leaves[li] = L;
 }
 
@@ -455,13 +457,15 @@ __global__ void k_leaf_geometry(GeomArgs a) {
     float p[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+      // the periodic image nearest the top cell; the FP32 copy decides (a
+      // particle lies within about one cell of its own, far from L/2)
       double rel = x[d] - (double)c[d] * B.w[d];
-      if (rel > 0.5 * B.L[d])
-        rel -= B.L[d];
-      else if (rel < -0.5 * B.L[d])
-        rel += B.L[d];
+      float rf = (float)rel;
+      if (fabsf(rf) > 0.5f * (float)B.L[d]) {
+        rel += rf > 0.f ? -B.L[d] : B.L[d];
+        rf = (float)rel;
+      }
       p[d] = (float)(rel - L.o[d]);
-      const float rf = (float)rel;
       lo[d] = fminf(lo[d], rf);
       hi[d] = fmaxf(hi[d], rf);
       out = fmaxf(out, fmaxf(-rf, rf - B.wf[d]));

@@ -65,6 +65,8 @@ struct Leaf {
   int start, count;
   int node, box;
   double o[3];       // leaf-cell origin relative to its top-cell origin
+  float of[3];       // o rounded to FP32 (box arithmetic with a pruning margin only)
+  int pad;
 };
 
 // One entry of a leaf's task list: the source leaf and the shift that maps
