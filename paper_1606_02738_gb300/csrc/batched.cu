@@ -810,10 +810,10 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; pass < a.max_iter; ++pass) {
       if (mode < 2 && __any_sync(0xffffffffu, need_filter)) {
-        // sub-cluster radius: its largest h x the stage skin, capped by Rg
+        // sub-cluster radius: its largest h x the list skin, capped by Rg
         float hm = has && !fin ? it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        rsub = fminf(hm * a.skin_stage, Rg);
+        rsub = fminf(hm * a.skin_list, Rg);
         ncand = filter_stage<false>(S.stage, nullptr, sr, blo, bhi, rsub, cand, kCandD, lane);
         need_filter = false;
         need_list = !fin;

@@ -726,8 +726,15 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &t
   return sync_check(c);
 }
 
-constexpr float kSkinStage = 1.15f;  // staged radius = 1.15 x the group's largest h
-constexpr float kSkinList = 1.05f;   // per-lane list radius = 1.05 x the lane's h
+// Radii of the batched density, as multiples of h from before the call: the
+// stage (group walk and staging) covers 1.06 x the group's largest h, a
+// warp's candidates 1.02 x its sub-cluster's largest h, a lane's list 1.02 x
+// its target's h. Steady steps start from h carried by the drift, so the
+// iteration rarely leaves these radii; when a target's h does, its warp
+// refilters or rebuilds its lists, and beyond the stage the target goes to
+// the third tier.
+constexpr float kSkinStage = 1.06f;
+constexpr float kSkinList = 1.02f;
 
 // Batched density: every particle whose group fits the stage and converges
 // inside the kernel is finished here; the rest keep done = 0 for the

@@ -588,7 +588,7 @@ struct BatchDensArgs {
   double n_ngb, tol, gamma;
   int max_iter;
   float skin_stage;      // stage radius factor (matches the list build)
-  float skin_list;       // per-lane list radius factor
+  float skin_list;       // per-lane list and sub-cluster candidate radius factor
   int kahan;             // compensated sums
   unsigned char *done;
   int *niter, *nngb;
