@@ -81,12 +81,20 @@ ORACLE_MAX_N = 2_000_000  # larger workloads: the oracle legs run the same recip
 
 def oracle_workload(name, scale, p):
     """The particle set the oracle legs time: the workload itself, or for sets
-    above ORACLE_MAX_N particles the same recipe and seed shrunk to about 1M
-    particles (the oracle's untimed set-up density of every particle would
-    otherwise take minutes). Returns (particles, note)."""
+    above ORACLE_MAX_N particles a part of about 1M particles (the oracle's
+    untimed set-up density of every particle would otherwise take minutes):
+    the first boxes of a multi-box set, else the same recipe and seed shrunk.
+    Returns (particles, note)."""
     if p.n <= ORACLE_MAX_N:
         return p, ""
-    q, _, _ = workload(name, scale * 1.0e6 / p.n)
+    target = ORACLE_MAX_N // 2
+    if p.n_boxes > 1:
+        import numpy as np
+        k = int(np.searchsorted(p.box_offsets, target, side="left"))
+        k = max(1, min(k, p.n_boxes))
+        q = p.subset_boxes(0, k)
+        return q, f" (the first {k} of its {p.n_boxes} boxes, {q.n} of {p.n} particles)"
+    q, _, _ = workload(name, scale * target / p.n)
     return q, f" (the {name} recipe shrunk from {p.n} to {q.n} particles)"
 
 

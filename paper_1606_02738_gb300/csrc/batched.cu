@@ -532,7 +532,7 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
       for (int f = incl - cnt; f < incl; ++f) tmap[f] = (unsigned char)lane;
       __syncwarp();
     }
-    constexpr int kU = 4;  // chunks whose loads are in flight together
+    constexpr int kU = FORCE ? 4 : 8;  // chunks in flight together (fewer: the force kernel spills)
     for (int f0 = 0; f0 < total; f0 += 32 * kU) {
       float4 q[kU], fj[kU];
       int jj[kU];

@@ -60,12 +60,16 @@ class ParticleSet:
         return slice(int(self.box_offsets[b]), int(self.box_offsets[b + 1]))
 
     def subset_box(self, b: int) -> "ParticleSet":
-        s = self.box_slice(b)
+        return self.subset_boxes(b, b + 1, name=f"{self.name}[box {b}]")
+
+    def subset_boxes(self, b0: int, b1: int, name: str | None = None) -> "ParticleSet":
+        """Boxes b0 .. b1-1 as a set of their own (the boxes never interact)."""
+        lo, hi = int(self.box_offsets[b0]), int(self.box_offsets[b1])
         return ParticleSet(
-            name=f"{self.name}[box {b}]", x=self.x[s].copy(), v=self.v[s].copy(),
-            m=self.m[s].copy(), u=self.u[s].copy(), h=self.h[s].copy(),
-            box=self.box[b:b + 1].copy(),
-            box_offsets=np.array([0, s.stop - s.start], dtype=np.int64),
+            name=name or f"{self.name}[boxes {b0}:{b1}]", x=self.x[lo:hi].copy(),
+            v=self.v[lo:hi].copy(), m=self.m[lo:hi].copy(), u=self.u[lo:hi].copy(),
+            h=self.h[lo:hi].copy(), box=self.box[b0:b1].copy(),
+            box_offsets=(self.box_offsets[b0:b1 + 1] - lo).astype(np.int64),
             gamma=self.gamma, n_ngb=self.n_ngb, meta=dict(self.meta))
 
 
