@@ -227,16 +227,16 @@ def hbm_peak_gbs() -> tuple[float, str]:
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def kernel_traffic(kernel: str, mode: str):
+def kernel_traffic(kernel: str, mode: str, workload_name: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    from a committed ncu capture of this kernel in this form, only while the
-    source files it was taken on are unchanged."""
+    from a committed ncu capture of this kernel in this form on this workload,
+    only while the source files it was taken on are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(f"{kernel}_{mode}")
     except (OSError, ValueError):
         return None
-    if not rec:
+    if not rec or rec.get("workload") != workload_name:
         return None
     if rec.get("source_sha") != source_sha(rec.get("sources", [])):
         return None
@@ -468,7 +468,7 @@ def run_ours(args, d: Dist):
                       "flops_per_launch": flops * ikey / n}
     dom = max(kern, key=lambda k: kern[k]["share_of_step"])
     roof = {"bound": "alu", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
-            "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom, args.mode),
+            "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom, args.mode, wname),
             "kernel": dom, "peak_source": peak_src,
             "flops_per_interaction": {"density": FLOPS_DENSITY, "force": FLOPS_FORCE},
             "kernels": kern}
