@@ -1,6 +1,7 @@
-"""Steps on a reused grid (SURVEY's incremental rebuild: the grid of the last
-regrid is kept while every particle stays within reach of its top cell; in
-the batched FP32 form such a step is one CUDA graph launch),
+"""Steps on a reused grid (incremental rebuild: as in Section 4.1, cells are
+rebuilt only when particles have strayed too far; the grid of the last regrid
+is kept while every particle stays within reach of its top cell, and in the
+batched FP32 form such a step is one CUDA graph launch),
 through the C ABI and against the FP64 oracle. A step whose particles moved
 too far is redone from its starting state on a new grid; the results must
 not depend on which path a step took."""
