@@ -295,6 +295,39 @@ def test_kdk_second_order_energy_and_momentum(oracle_lib):
     assert np.abs(m1).max() < 1e-14 and np.abs(m2).max() < 1e-14
 
 
+def _reversal_error(dt, t_end, p):
+    """Run to t_end, reverse v (and du/dt, which is odd in v), run back: the
+    distance from the starting x, -v and u."""
+    s = oracle.State.from_particles(p)
+    oracle.evaluate(s)
+    x0, v0, u0 = s.x.copy(), s.v.copy(), s.u.copy()
+    n = int(round(t_end / dt))
+    for _ in range(n):
+        oracle.kdk_step(s, dt)
+    s.v = -s.v
+    s.dudt = -s.dudt
+    for _ in range(n):
+        oracle.kdk_step(s, dt)
+    d = s.x - x0
+    d -= s.box[0] * np.round(d / s.box[0])
+    return np.abs(d).max(), np.abs(s.v + v0).max(), np.abs(s.u - u0).max()
+
+
+def test_kdk_time_reversal(oracle_lib):
+    """Kick-drift-kick retraces its path when the velocities are reversed: the
+    half kicks and the drift are symmetric in time, and only the prediction
+    of v and u for the mid-step force (with the rates of the step's start)
+    breaks the symmetry, by an amount that falls as dt^3 over a fixed time.
+    A drift with the old v, a closing kick with the old a, or a one-sided
+    energy update returns with an error of lower order."""
+    p = inputs.lattice(10, jitter=0.1, sigma_v=0.05, h_factor=2.3)
+    e1 = _reversal_error(0.0025, 0.04, p)
+    e2 = _reversal_error(0.00125, 0.04, p)
+    for a, b in zip(e1, e2):
+        assert 6.0 < a / b < 10.0, (e1, e2)
+    assert e1[0] < 1e-8 and e1[1] < 1e-6 and e1[2] < 1e-5
+
+
 # ------------------------------------------------------------ errors
 
 def test_box_too_small_error(oracle_lib):
