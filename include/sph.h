@@ -210,8 +210,10 @@ int sph_density(sph_ctx *ctx);
 int sph_force(sph_ctx *ctx);
 
 /* n_steps kick-drift-kick steps with global time step dt (> 0): half kick,
- * drift (FP64 positions, periodic wrap), grid rebuild, density, force with
- * velocities and energies predicted to the end of the step, half kick.
+ * drift (FP64 positions, periodic wrap; h carried along as the starting
+ * guess of the next iteration, h exp(-dt (du/dt) / (3 (gamma - 1) u))), grid
+ * rebuild or reuse (reuse_grid), density, force with velocities and
+ * energies predicted to the end of the step, half kick.
  * Requires sph_force on the current state first (SPH_ESTATE). Errors as
  * sph_density, plus SPH_ENONPHYSICAL when some u becomes <= 0. */
 int sph_step(sph_ctx *ctx, double dt, int n_steps);
