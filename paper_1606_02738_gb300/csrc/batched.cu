@@ -1,24 +1,26 @@
-// batched.cu -- the batched interaction form: one warp per target group of up
-// to 32 consecutive particles of a top cell, candidates staged once in shared
-// memory, per-lane compacted neighbour lists, and the smoothing-length
-// iteration run inside the kernel (Section 2 density and force, with the
-// ghost task of Section 3.1 fused into the density kernel).
+// batched.cu -- the batched interaction form: one block of 4 warps per target
+// group of up to 32 consecutive particles of a top cell, candidates staged
+// once in shared memory, per-lane compacted neighbour lists, and the
+// smoothing-length iteration run inside the kernel (Section 2 density and
+// force, with the ghost task of Section 3.1 fused into the density kernel).
 //
 // Per group:
 //   1. walk the octrees of the 27 neighbouring top cells for the source leaves
 //      whose box lies within the group's radius (the refined pair tasks);
 //   2. stage, into shared memory, every source particle within that radius of
-//      the group's bounding box, shifted into the group's frame (one test per
-//      candidate per warp);
-//   3. each lane keeps the staged particles within its own radius in a list of
-//      16-bit indices, so the passes over h, and the force, touch only those;
-//   4. density: sums, FP64 Newton step on ln N(ln h), repeat until every lane
-//      converged (list rebuilt from the stage when an h outgrows it);
-//      force: one pass over the list.
-// A group whose candidates overflow the shared-memory stage, or whose h
-// outgrows the staged radius, is left to the per-pass form (the host runs it
-// for every particle not finished here), so results never depend on the
-// capacities.
+//      the group's bounding box, shifted into the group's frame;
+//   3. each warp keeps the staged particles within reach of its sub-cluster of
+//      8 targets, and each lane keeps its share of its target's neighbours in
+//      a list of 16-bit stage indices, so the passes over h, and the force,
+//      touch only those;
+//   4. density: sums, Newton step on ln N(ln h) (h in FP32, acceptance test in
+//      FP64), repeated until every lane converged (candidates and lists rebuilt
+//      from the stage when an h outgrows them); force: one pass over the lists.
+// Groups whose stage overflows are staged again by each target's own radius
+// (second tier, larger stage); targets that overflow that, or whose h outgrows
+// the staged radius, are finished one warp per target by a direct walk of the
+// octrees (third tier). Only a target the third tier cannot finish is left to
+// the per-pass form, so results never depend on the capacities.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -390,13 +392,14 @@ void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
 // ------------------------------------------------------------ kernels
 //
 // One block of kNW warps per group. All warps stage the group's candidates
-// together (a count pass, then per-warp shares laid out in warp order: the
-// stage order never depends on timing). Then each warp works alone on a
-// sub-cluster of 8 consecutive targets (compact: consecutive in octree
-// order): it keeps the staged entries within its sub-cluster's radius, and
-// gives every target 4 lanes, lane s of a target handling every 4th of those
-// entries; the 4 partial sums are combined by shuffles in fixed order, so the
-// 4 lanes hold identical totals and take identical h steps.
+// together, in one pass, each warp into its own segment of the stage in the
+// order it found them (the stage order never depends on timing). Then each
+// warp works alone on a sub-cluster of 8 consecutive targets (compact:
+// consecutive in octree order): it keeps the staged entries within its
+// sub-cluster's radius, and gives every target 4 lanes, lane s of a target
+// handling every 4th of those entries; the 4 partial sums are combined by
+// shuffles in fixed order, so the 4 lanes hold identical totals and take
+// identical h steps.
 
 constexpr int kNW = 4;           // warps per block, one group per block
 constexpr int kSub = 8;          // targets per warp
@@ -418,7 +421,7 @@ constexpr int force_cand(int ns) { return ns == kStageF ? kCandF : kCandFL; }
 constexpr int kLaneD = 32;       // density list entries per lane (tile 0)
 constexpr int kLaneF = 28;       // force list entries per lane (tile 0)
 // list entries per lane for a first-tier stage size (tile 1 and the second
-// tier hold longer lists: clumped inputs put more particles inside 1.05 h)
+// tier hold longer lists: clumped inputs put more particles inside the list radius)
 constexpr int dens_lane(int ns) { return ns == kStageD ? kLaneD : 48; }
 constexpr int force_lane(int ns) { return ns == kStageF ? kLaneF : 32; }
 static_assert(kLaneD % 4 == 0 && kLaneF % 4 == 0, "lists are padded to multiples of 4");
