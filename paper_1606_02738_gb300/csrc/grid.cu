@@ -14,7 +14,8 @@
 //       node), down to leaves of at most n_split particles.
 //   Task lists: for every target leaf, the source leaves whose bounding box
 //       lies within the interaction radius, found by walking the octrees of
-//       the 27 neighbouring top cells (the refined self/pair task set).
+//       the 27 neighbouring top cells (the refined self/pair task set), one
+//       warp per target leaf, breadth first.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -4,11 +4,18 @@
 // ghost -> force -> integrator, mapped to stream-ordered kernel launches):
 //   sph_init     wrap positions, build grid (A1), split cells (A2), gather
 //                the particle store into leaf order, leaf geometry.
-//   sph_density  repeat { leaf h maxima, active leaves, density task lists,
-//                density gather (A4), ghost h update (A5) } until every h
-//                has converged; rebuild the grid when an h outgrows it.
-//   sph_force    force task lists, force gather (A6).
-//   sph_step     kick + drift, regrid, density, force (predicted v, u), kick.
+//   sph_density  batched form (default): group frames and h maxima, group
+//                walk, the three density tiers with the h iteration inside
+//                (A4, A5), no host round trip between them; per-pass form,
+//                and any target the batched tiers leave: repeat { leaf h
+//                maxima, active leaves, density task lists, density gather
+//                (A4), ghost h update (A5) } until every h has converged.
+//                The grid is rebuilt when an h outgrows it.
+//   sph_force    batched: group h maxima, group walk, the three force tiers
+//                (A6); per-pass: force task lists, force gather.
+//   sph_step     kick + drift, position refresh on the reused grid (or a
+//                regrid), density, force (predicted v, u), kick, grid check;
+//                steady batched steps replay one captured CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
