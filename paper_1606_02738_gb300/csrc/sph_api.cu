@@ -96,7 +96,7 @@ struct sph_ctx {
   int reuse_streak = 0;            // steps run in a row on the current grid
   int regrids_in_step = 0;
   long long grid_stamp = 0;        // bumped by every regrid (sizes, buffers, store swap)
-  // steady steps as one CUDA graph (batched FP32 form on a reused grid)
+  // steady steps as one CUDA graph (batched form on a reused grid)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
@@ -1102,7 +1102,7 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
   return read_counters(c);
 }
 
-// Everything a step on the reused grid issues in the batched FP32 form, with
+// Everything a step on the reused grid issues in the batched form, with
 // no host reads: the body of the captured graph. Mirrors step_once(reuse).
 int enqueue_steady_step(sph_ctx *c, double dt) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));

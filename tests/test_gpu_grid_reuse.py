@@ -1,7 +1,7 @@
 """Steps on a reused grid (incremental rebuild: as in Section 4.1, cells are
 rebuilt only when particles have strayed too far; the grid of the last regrid
 is kept while every particle stays within reach of its top cell, and in the
-batched FP32 form such a step is one CUDA graph launch),
+batched form such a step is one CUDA graph launch),
 through the C ABI and against the FP64 oracle. A step whose particles moved
 too far is redone from its starting state on a new grid; the results must
 not depend on which path a step took."""
@@ -35,11 +35,16 @@ def _steps(p, n, dt, **kw):
     return out
 
 
-@pytest.mark.parametrize("mode", [sph.SPH_MODE_BATCHED, sph.SPH_MODE_PLAIN])
-def test_sod_steps_on_reused_grid_match_oracle(mode):
+@pytest.mark.parametrize("mode,tile,precision", [
+    (sph.SPH_MODE_BATCHED, 0, sph.SPH_PREC_FP32), (sph.SPH_MODE_PLAIN, 0, sph.SPH_PREC_FP32),
+    (sph.SPH_MODE_BATCHED, 1, sph.SPH_PREC_FP32), (sph.SPH_MODE_BATCHED, 0, sph.SPH_PREC_KAHAN)],
+    ids=["batched", "plain", "batched-tile1", "batched-kahan"])
+def test_sod_steps_on_reused_grid_match_oracle(mode, tile, precision):
+    """Steps on the reused grid, the batched ones from the second on as one CUDA
+    graph (both tiles, plain and compensated sums), against the oracle."""
     p = inputs.sod(nx_left=96, n_yz_left=24, nx_right=48, n_yz_right=12)
     dt, n = 2e-3, 6
-    g = _steps(p, n, dt, mode=mode)
+    g = _steps(p, n, dt, mode=mode, tile=tile, precision=precision)
     st = g["stats"]
     assert st["reused_steps"] >= n - 2, st["reused_steps"]
     if mode == sph.SPH_MODE_BATCHED:  # from a grid's second reused step on: one CUDA graph
