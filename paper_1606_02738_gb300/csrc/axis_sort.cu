@@ -15,9 +15,11 @@
 // sorted range whose keys fall inside [min_i d_i - R, max_i d_i + R] (shifted
 // into the source frame); |d_i - d_j| <= |x_i - x_j| makes the cut exact.
 //
-// One warp per leaf; ranks are counted against tiles of keys in shared
-// memory (leaves hold <= n_split particles except at the depth limit; any
-// count is handled, in O(count^2) compares).
+// One warp per leaf; every particle counts the keys below its own (ranks,
+// O(count^2) compares). A leaf of at most kSortMax particles (every leaf but
+// those at the depth limit) has its positions read once into shared memory
+// and each direction's keys formed once there; larger leaves are ranked
+// against tiles of keys read from global memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,13 +29,39 @@ namespace sph {
 
 constexpr int kSortWarps = 4;
 constexpr int kSortTile = 256;
+constexpr int kSortMax = 256;  // leaves ranked from shared memory
 
 __global__ void __launch_bounds__(kSortWarps * 32) k_axis_sort(AxisSortArgs a) {
-  __shared__ float tile[kSortWarps][kSortTile];
+  __shared__ float4 pos_all[kSortWarps][kSortMax];
+  __shared__ float tile_all[kSortWarps][kSortTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int li = blockIdx.x * kSortWarps + warp;
   if (li >= a.n_leaves) return;  // warp-uniform
   const Leaf L = a.leaves[li];
+  float *tile = tile_all[warp];
+  if (L.count <= kSortMax) {
+    float4 *pos = pos_all[warp];
+    for (int p = lane; p < L.count; p += 32) pos[p] = a.pm[L.start + p];
+    for (int k = 0; k < kAxes; ++k) {
+      const float3 e = axis_vec(k);
+      __syncwarp();  // pos written; the previous direction's ranking is done with tile
+      for (int p = lane; p < L.count; p += 32) tile[p] = axis_key(pos[p], e);
+      __syncwarp();
+      float *key_out = a.skey + (size_t)k * a.n + L.start;
+      int *idx_out = a.sidx + (size_t)k * a.n + L.start;
+      for (int p = lane; p < L.count; p += 32) {
+        const float kp = tile[p];
+        int rank = 0;
+        for (int q = 0; q < L.count; ++q) {
+          const float kq = tile[q];
+          rank += (kq < kp || (kq == kp && q < p)) ? 1 : 0;
+        }
+        key_out[rank] = kp;
+        idx_out[rank] = p;
+      }
+    }
+    return;
+  }
   for (int k = 0; k < kAxes; ++k) {
     const float3 e = axis_vec(k);
     float *key_out = a.skey + (size_t)k * a.n + L.start;
@@ -46,10 +74,10 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_axis_sort(AxisSortArgs a) {
       for (int qb = 0; qb < L.count; qb += kSortTile) {
         const int nq = min(kSortTile, L.count - qb);
         __syncwarp();
-        for (int q = lane; q < nq; q += 32) tile[warp][q] = axis_key(a.pm[L.start + qb + q], e);
+        for (int q = lane; q < nq; q += 32) tile[q] = axis_key(a.pm[L.start + qb + q], e);
         __syncwarp();
         for (int q = 0; q < nq; ++q) {
-          const float kq = tile[warp][q];
+          const float kq = tile[q];
           rank += (kq < kp || (kq == kp && qb + q < p)) ? 1 : 0;
         }
       }
