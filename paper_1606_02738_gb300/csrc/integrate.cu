@@ -127,13 +127,22 @@ void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *o
 // the step as h exp(-dt (du/dt) / (3 (gamma-1) u)). Only the guess moves: the
 // density stage still iterates h to its own root (Section 2, constant
 // neighbour number), so results do not depend on it beyond the tolerance.
+template <bool SAVE>
 __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int nb,
-                             float gm1, float *hf, DevCounters *ctr) {
+                             float gm1, float *hf, StoreArrays save, DevCounters *ctr) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float hdt = (float)(0.5 * dt);
   const float4 a = st.acc[s];
   float4 v = st.vu[s];
+  if (SAVE) {
+    save.x0[s] = st.x0[s];
+    save.x1[s] = st.x1[s];
+    save.x2[s] = st.x2[s];
+    save.h[s] = st.h[s];
+    save.vu[s] = v;
+    save.acc[s] = a;
+  }
   if (v.w > 0.f && a.w != 0.f) {
     const float e = fminf(fmaxf(-(float)dt * a.w / (3.f * gm1 * v.w), -0.2f), 0.2f);
     const double h = st.h[s] * (double)expf(e);
@@ -156,9 +165,15 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
 }
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
-                       double gamma, float *hf, DevCounters *ctr, cudaStream_t s) {
-  k_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, (float)(gamma - 1.0),
-                                                 hf, ctr);
+                       double gamma, float *hf, const StoreArrays *save, DevCounters *ctr,
+                       cudaStream_t s) {
+  const float gm1 = (float)(gamma - 1.0);
+  if (save)
+    k_kick_drift<true><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf, *save,
+                                                       ctr);
+  else
+    k_kick_drift<false><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf,
+                                                        StoreArrays{}, ctr);
   note_launch();
 }
 

@@ -1062,8 +1062,10 @@ int refresh_grid(sph_ctx *c) {
   return sync_check(c);
 }
 
-// The state a step starts from (positions, h, v and u, accelerations), kept
-// in the second store copy so a step on a reused grid can be redone.
+// Copies the state a step starts from (positions, h, v and u, accelerations)
+// between the store and its second copy: kick-drift saves it into the second
+// copy as it reads it, and a step on a reused grid that has to be redone is
+// restored from there.
 void copy_step_state(sph_ctx *c, const StoreArrays &from, const StoreArrays &to) {
   const size_t n = (size_t)c->n;
   cudaMemcpyAsync(to.x0, from.x0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -1080,9 +1082,9 @@ void copy_step_state(sph_ctx *c, const StoreArrays &from, const StoreArrays &to)
 int step_once(sph_ctx *c, double dt, bool reuse) {
   c->regrids_in_step = 0;
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
-  if (reuse) copy_step_state(c, c->st, c->st2);
   tic(c, kInteg);
-  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, c->ctr, c->stream);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf,
+                    reuse ? &c->st2 : nullptr, c->ctr, c->stream);
   toc(c, kInteg);
   c->density_valid = false;
   c->force_valid = false;
@@ -1106,9 +1108,9 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
 // no host reads: the body of the captured graph. Mirrors step_once(reuse).
 int enqueue_steady_step(sph_ctx *c, double dt) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
-  copy_step_state(c, c->st, c->st2);
   tic(c, kInteg);
-  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, c->ctr, c->stream);
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, &c->st2, c->ctr,
+                    c->stream);
   toc(c, kInteg);
   tic(c, kGrid);
   CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
