@@ -129,9 +129,12 @@ void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *o
 // neighbour number), so results do not depend on it beyond the tolerance.
 template <bool SAVE>
 __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int nb,
-                             float gm1, float *hf, StoreArrays save, DevCounters *ctr) {
+                             float gm1, float *hf, StoreArrays save, unsigned char *done,
+                             unsigned char *fdone, DevCounters *ctr) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
+  if (done) done[s] = 0;
+  if (fdone) fdone[s] = 0;
   const float hdt = (float)(0.5 * dt);
   const float4 a = st.acc[s];
   float4 v = st.vu[s];
@@ -165,15 +168,15 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
 }
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
-                       double gamma, float *hf, const StoreArrays *save, DevCounters *ctr,
-                       cudaStream_t s) {
+                       double gamma, float *hf, const StoreArrays *save, unsigned char *done,
+                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s) {
   const float gm1 = (float)(gamma - 1.0);
   if (save)
     k_kick_drift<true><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf, *save,
-                                                       ctr);
+                                                       done, fdone, ctr);
   else
     k_kick_drift<false><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf,
-                                                        StoreArrays{}, ctr);
+                                                        StoreArrays{}, done, fdone, ctr);
   note_launch();
 }
 

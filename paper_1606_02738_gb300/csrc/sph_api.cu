@@ -932,7 +932,9 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
 }
 
 // The kernels of the batched force, no host reads.
-int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force) {
+// `fdone_clear`: the force finished flags are already zero (a steady step
+// clears them in kick-drift).
+int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool fdone_clear = false) {
   if (!c->groups_valid) TRY(build_groups(c));
   GroupBuildArgs gb = group_args(c);
   launch_group_hmax(gb, c->stream);
@@ -944,7 +946,7 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
   CUDA_TRY(cudaMemsetAsync(&c->ctr->queued2[1], 0, sizeof(int), c->stream));
-  CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
+  if (!fdone_clear) CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
   fa.groups = as<Group>(c->groups);
@@ -1084,7 +1086,7 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
   tic(c, kInteg);
   launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf,
-                    reuse ? &c->st2 : nullptr, c->ctr, c->stream);
+                    reuse ? &c->st2 : nullptr, nullptr, nullptr, c->ctr, c->stream);
   toc(c, kInteg);
   c->density_valid = false;
   c->force_valid = false;
@@ -1107,10 +1109,13 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
 // Everything a step on the reused grid issues in the batched form, with
 // no host reads: the body of the captured graph. Mirrors step_once(reuse).
 int enqueue_steady_step(sph_ctx *c, double dt) {
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream));
   tic(c, kInteg);
-  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, &c->st2, c->ctr,
-                    c->stream);
+  // also clears the density and force finished flags (the batched tiers keep
+  // their h brackets in registers, so nothing else of the iteration state
+  // needs resetting)
+  launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, &c->st2, c->done,
+                    c->fdone, c->ctr, c->stream);
   toc(c, kInteg);
   tic(c, kGrid);
   CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
@@ -1123,12 +1128,10 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   // leaf-density estimate); the h maxima of the last force still bound it to
   // within the stage skin, and a target whose h leaves its staged radius is
   // finished by the third tier
-  launch_reset_iteration(c->done, c->niter, c->st.hlo, c->st.hhi, c->fprev, c->n, c->stream);
-  CUDA_TRY(cudaMemsetAsync(c->ctr, 0, offsetof(DevCounters, step_status), c->stream));
   launch_group_geometry(group_args(c), c->stream);
   c->groups_geom_valid = true;
   TRY(enqueue_density_batched(c, c->st.vu_pred, true));
-  TRY(enqueue_force_batched(c, c->st.vu_pred));
+  TRY(enqueue_force_batched(c, c->st.vu_pred, true));
   tic(c, kInteg2);
   launch_kick(c->st, c->n, dt, c->ctr, c->stream);
   toc(c, kInteg2);

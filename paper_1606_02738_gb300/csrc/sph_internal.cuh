@@ -643,10 +643,12 @@ void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *o
 void launch_wrap_cell_keys_from_caller(const double *x, const BoxDev *boxes, int n_boxes, int n,
                                        double *x0, double *x1, double *x2, cudaStream_t s);
 // save: when not null, the step's starting x, h, (v, u) and (a, du/dt) are
-// copied there as they are read (the state a redone step restarts from)
+// copied there as they are read (the state a redone step restarts from);
+// done / fdone: when not null, the per-particle finished flags of the density
+// and force are cleared on the way
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
-                       double gamma, float *hf, const StoreArrays *save, DevCounters *ctr,
-                       cudaStream_t s);
+                       double gamma, float *hf, const StoreArrays *save, unsigned char *done,
+                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s);
 void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s);
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
 void launch_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of, cudaStream_t s);
