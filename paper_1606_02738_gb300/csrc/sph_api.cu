@@ -932,21 +932,24 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
 }
 
 // The kernels of the batched force, no host reads.
-// `fdone_clear`: the force finished flags are already zero (a steady step
-// clears them in kick-drift).
-int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool fdone_clear = false) {
+// `steady`: called from a steady step, whose start zeroed every counter and
+// whose kick-drift cleared the force finished flags (the density writes none
+// of the force's counters; any fallback there redoes the step).
+int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool steady = false) {
   if (!c->groups_valid) TRY(build_groups(c));
   GroupBuildArgs gb = group_args(c);
   launch_group_hmax(gb, c->stream);
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
   TRY(build_group_lists(c, true, 1.0f, c->gf_off, c->gf_tasks));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
-  CUDA_TRY(cudaMemsetAsync(&c->ctr->queued2[1], 0, sizeof(int), c->stream));
-  if (!fdone_clear) CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
+  if (!steady) {
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->queued2[1], 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
+  }
   BatchForceArgs fa{};
   fa.n_groups = c->n_groups;
   fa.groups = as<Group>(c->groups);
