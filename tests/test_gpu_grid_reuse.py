@@ -1,5 +1,5 @@
 """Steps on a reused grid (incremental rebuild: as in Section 4.1, cells are
-rebuilt only when particles have strayed too far; the grid of the last regrid
+rebuilt only when particles have moved too far from them; the grid of the last regrid
 is kept while every particle stays within reach of its top cell, and in the
 batched form such a step is one CUDA graph launch),
 through the C ABI and against the FP64 oracle. A step whose particles moved
