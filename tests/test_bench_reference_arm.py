@@ -57,3 +57,16 @@ def test_reference_arm_two_ranks_only_rank0_reports():
     lines0 = [ln for ln in outs[0][0].splitlines() if ln.strip().startswith("{")]
     assert len(lines0) == 1 and json.loads(lines0[0])["impl"] == "reference"
     assert outs[1][0].strip() == ""
+
+
+def test_gpu_arm_refuses_to_run_without_cuda():
+    """Without a CUDA device the benchmark's own arm stops with an error: the
+    CUDA path has no CPU fallback."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "CUDA" in (r.stderr + r.stdout) and not r.stdout.strip().startswith("{")
