@@ -65,7 +65,15 @@ extern "C" {
 #define SPH_NITER 10 /* int32  [N]    density passes the particle's h needed */
 #define SPH_NFORCE 11 /* int32 [N]    #{j != i : r_ij < max(h_i, h_j)} */
 #define SPH_M 12     /* float  [N]    masses */
-#define SPH_NFIELDS 13
+#define SPH_CELL 13  /* int32  [N][4] the grid cell the particle was binned into at the last
+                        regrid (Section 3.1 cells): integer coordinates (ix, iy, iz) of its
+                        top cell in its box, ix = floor(x / w_x) exactly for the FP64 x
+                        (wrapped into [0, L)) and the FP64 width w_x of sph_grid, and, 4th,
+                        the level of its octree leaf inside that top cell (0: the top cell) */
+#define SPH_LEAF_CELL 14 /* int32 [N][3] integer coordinates of the particle's octree leaf
+                        cell (edge w / 2^level) inside its top cell at the last regrid: the
+                        leading `level` bits of floor((x - ix w) x (1 / w) x 1024) per axis */
+#define SPH_NFIELDS 15
 
 /* ---- interaction-kernel forms ---- */
 #define SPH_MODE_PLAIN 0   /* one launch per density pass, host-driven h iteration */
@@ -259,6 +267,13 @@ int sph_get_pair_order(sph_ctx *ctx, int axis, int32_t *order_out, int32_t *leaf
  * Errors: SPH_EINVAL (null tflops_out, bad device), SPH_ENOMEM, SPH_ECUDA. */
 int sph_fp32_peak(int device, double *tflops_out, double *ms_out);
 
+/* Top grid of box `box` (0 <= box < n_boxes) as of the last regrid (Section
+ * 3.1: cells no smaller than the largest smoothing length): cells per axis
+ * (n_out, host int32[3]) and the FP64 cell widths w = L / n (w_out, host
+ * double[3]; either may be NULL). Errors: SPH_EINVAL (box out of range),
+ * SPH_ESTATE (no particles loaded). */
+int sph_grid(const sph_ctx *ctx, int box, int32_t *n_out, double *w_out);
+
 /* Counters of the last density/force calls (synchronises the stream). */
 int sph_stats(sph_ctx *ctx, sph_stats_t *out);
 
@@ -274,28 +289,41 @@ void sph_destroy(sph_ctx *ctx);
  * framework that owns the whole GPU through its own memory pool, or code
  * where a cudaMalloc/cudaFree (which can also synchronise the device) is not
  * allowed. The regular entry points allocate a particle store and task lists;
- * this one allocates nothing. It runs the same density sums and the same
- * smoothing-length iteration as sph_density for ONE periodic box of at most
- * SPH_NOALLOC_MAX_PARTICLES particles, finding neighbours by scanning all
- * particles (minimum image), and keeps its per-particle scratch (~0.9 MB) in
- * a fixed device array that exists on every device that loads the library
- * until the process exits.
+ * this one allocates nothing itself. It runs the same density sums and the
+ * same smoothing-length update rule as the per-pass density form for ONE
+ * periodic box of at most SPH_NOALLOC_MAX_PARTICLES particles, finding
+ * neighbours by scanning all particles (minimum image), and keeps its
+ * per-particle scratch (~0.9 MB) in a fixed device array of this library's
+ * CUDA module.
  *
  *   n          particles, 1 <= n <= SPH_NOALLOC_MAX_PARTICLES (else SPH_EINVAL)
  *   box_len    host, 3 edge lengths of the periodic box (> 0)
  *   x          device, double [n][3] positions (inside or outside the box)
- *   m          device, float [n] masses
+ *   m          device, float [n] masses (> 0)
  *   h0         device, double [n] initial smoothing-length guesses (> 0)
  *   n_ngb, h_tol, max_iter   as in sph_params
  *   h_out      device, double [n]: converged h
- *   rho_out    device, float [n]: density, Eq. (rho)
+ *   rho_out    device, float [n]: density, the same sum as sph_density's
  *   omega_out  device, float [n]: Omega = 1 + h/(3 rho) drho/dh
  *   cuda_stream  cudaStream_t of the work (NULL: legacy default stream)
- * Returns SPH_OK, SPH_EINVAL, SPH_ECUDA, SPH_EBOXTOOSMALL, SPH_ENONPHYSICAL
- * or SPH_ENOTCONVERGED; synchronises the stream once per iteration pass.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make it before any stream capture. All calls share
- * the one scratch array: calls whose work overlaps on the GPU race on it. */
+ * Returns SPH_OK, SPH_EINVAL (bad arguments, or some m <= 0, h0 <= 0 or a
+ * non-finite x, m, h0), SPH_ECUDA, SPH_EBOXTOOSMALL, SPH_ENONPHYSICAL or
+ * SPH_ENOTCONVERGED.
+ *
+ * Memory: the scratch array is loaded with the module, on each device that
+ * uses the library: at context creation under CUDA_MODULE_LOADING=EAGER,
+ * otherwise (lazy loading, the CUDA default) when the module is first used
+ * on that device, which can be this call's first call. Make one warm-up call
+ * per device (or run with CUDA_MODULE_LOADING=EAGER) before relying on "no
+ * allocation"; the array then stays until the process exits. The first call
+ * on a device also looks up the array's device address
+ * (cudaGetSymbolAddress).
+ *
+ * Synchronisation: the call copies a status word to the host and
+ * synchronises the stream after every iteration pass, so it cannot be
+ * captured into a CUDA graph. All calls share the one scratch array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it. */
 #define SPH_NOALLOC_MAX_PARTICLES 16384
 int sph_density_noalloc(int n, const double *box_len, const double *x, const float *m,
                         const double *h0, double n_ngb, double h_tol, int max_iter,

@@ -9,20 +9,27 @@
 // particle store and task lists; this one keeps its per-particle scratch in a
 // fixed, file-scope __device__ array instead.
 //
-// Method: the same sums and the same smoothing-length update as the regular
-// density stage, but neighbours are found by scanning every particle of the
-// box (all pairs, minimum image), which is what makes a fixed-size scratch
-// possible; hence the particle cap SPH_NOALLOC_MAX_PARTICLES.
+// Method: the same sums and the same smoothing-length update rule as the
+// per-pass density form (h_newton_step, FP64 h and bracket), but neighbours
+// are found by scanning every particle of the box (all pairs, minimum image),
+// which is what makes a fixed-size scratch possible; hence the particle cap
+// SPH_NOALLOC_MAX_PARTICLES.
 //
-// Scratch: `g_na` below (about 0.9 MB) is allocated by the CUDA runtime when
-// the library is loaded, on every device that loads it, and lives until the
-// process exits. It is shared by all calls: the kernels clear what must start
-// at zero, and two calls whose work overlaps on the GPU (different streams,
-// or different host threads without ordering) race on it and give wrong
-// results. Host code cannot use the symbol as a device address, so the
+// Scratch: `g_na` below (about 0.9 MB) belongs to this library's CUDA module.
+// The module, and with it the array, is loaded into a device's context when
+// that context first needs it: at context creation when the process runs with
+// CUDA_MODULE_LOADING=EAGER, otherwise (lazy loading, the default of recent
+// CUDA releases) at the first use of anything in the module on that device,
+// which may be this entry point's first call. That first load is the one
+// allocation involved, made by the CUDA runtime; a caller that must see no
+// allocation at all makes one warm-up call per device (or sets
+// CUDA_MODULE_LOADING=EAGER) before it relies on that. The array then lives
+// until the process exits. It is shared by all calls: the kernels clear what
+// must start at zero, and two calls whose work overlaps on the GPU (different
+// streams, or different host threads without ordering) race on it and give
+// wrong results. Host code cannot use the symbol as a device address, so the
 // first call on each device asks the runtime for the array's device address
-// (cudaGetSymbolAddress) and caches it; make that first call before any
-// stream capture begins.
+// (cudaGetSymbolAddress) and caches it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,6 +60,8 @@ static __device__ __align__(256) NaScratch g_na;
 struct NaArgs {
   int n;
   double L[3];
+  double iL[3];  // 1 / L (minimum image by a product, no FP64 division per pair)
+  double hcap;   // largest allowed h: min(L) / (3 (1 + 1e-6)), as the regular path
   const double *x;
   const float *m;
   double n_ngb, tol;
@@ -62,6 +71,9 @@ struct NaArgs {
   float *rho_out, *omega_out;
 };
 
+// Iteration state from the caller's guesses; h0 <= 0, m <= 0 or a
+// non-finite x, h0 or m raises kErrInvalidInput (the call then returns
+// SPH_EINVAL before any density pass).
 __global__ void k_na_init(NaArgs a, const double *h0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -69,11 +81,17 @@ __global__ void k_na_init(NaArgs a, const double *h0) {
     a.s->unconverged = 0;
   }
   if (i >= a.n) return;
-  a.s->h[i] = h0[i];
+  const double h = h0[i];
+  const float m = a.m[i];
+  const double x0 = a.x[3 * (size_t)i], x1 = a.x[3 * (size_t)i + 1], x2 = a.x[3 * (size_t)i + 2];
+  const bool ok = h > 0.0 && isfinite(h) && m > 0.f && isfinite(m) && isfinite(x0) &&
+                  isfinite(x1) && isfinite(x2);
+  if (!ok) atomicOr(&a.s->status, kErrInvalidInput);
+  a.s->h[i] = ok ? h : 1.0;
   a.s->lo[i] = 0.0;
-  a.s->hi[i] = 1e308;
+  a.s->hi[i] = 1e308;  // open bracket, as HIter expects
   a.s->fprev[i] = __int_as_float(0x7f800000);
-  a.s->done[i] = 0;
+  a.s->done[i] = ok ? 0 : 1;
 }
 
 // All-pairs density sums at the current h of every unfinished particle.
@@ -104,9 +122,9 @@ __global__ void __launch_bounds__(kNaThreads) k_na_sums(NaArgs a) {
     const int nj = min(kNaThreads, a.n - base);
     for (int k = 0; k < nj; ++k) {
       double d0 = xi - sx[k], d1 = yi - sy[k], d2 = zi - sz[k];
-      d0 -= a.L[0] * rint(d0 / a.L[0]);
-      d1 -= a.L[1] * rint(d1 / a.L[1]);
-      d2 -= a.L[2] * rint(d2 / a.L[2]);
+      d0 = fma(-a.L[0], rint(d0 * a.iL[0]), d0);
+      d1 = fma(-a.L[1], rint(d1 * a.iL[1]), d1);
+      d2 = fma(-a.L[2], rint(d2 * a.iL[2]), d2);
       const float dx = (float)d0, dy = (float)d1, dz = (float)d2;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (r2 < h2) {
@@ -125,55 +143,37 @@ __global__ void __launch_bounds__(kNaThreads) k_na_sums(NaArgs a) {
   if (act) a.s->sums[i] = make_float4(sw, sdw, smw, smdh);
 }
 
-// Smoothing-length update (the same rule as the regular ghost step) and,
-// once converged, rho and Omega.
+// Smoothing-length update by h_newton_step (the rule of the per-pass ghost
+// kernel: Newton on ln N(ln h) inside the bisection bracket, FP64 h) and,
+// once converged, rho and Omega (FP64 from the FP32 sums).
 __global__ void k_na_update(NaArgs a, int pass) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n || a.s->done[i]) return;
-  const double h = a.s->h[i];
   const float4 s = a.s->sums[i];
-  const double N = (32.0 / 3.0) * (double)s.x;
-  const double dN = -(32.0 / (3.0 * h)) * (double)s.y;
-  const double f = N - a.n_ngb;
-  bool conv = fabs(f) <= a.tol * a.n_ngb;
+  HIter it;
+  it.start(a.s->h[i], a.s->lo[i], a.s->hi[i], a.s->fprev[i]);
+  const double h = it.h;
+  int st = 0;
+  const bool conv = h_newton_step(it, s.x, s.y, a.n_ngb, a.tol * a.n_ngb, a.hcap, &st);
+  if (st) atomicOr(&a.s->status, st);
   if (!conv) {
-    double lo = a.s->lo[i], hi = a.s->hi[i];
-    if (f < 0.0)
-      lo = h;
-    else
-      hi = h;
-    const double s_ln = (N > 0.0 && dN > 0.0) ? h * dN / N : 0.0;
-    double hn = s_ln > 0.0 ? h * exp(log(a.n_ngb / N) / s_ln) : 2.0 * h;
-    hn = fmin(fmax(hn, 0.125 * h), 2.0 * h);
-    if (hi < 1e300 && (!(hn > lo && hn < hi) || fabs(f) > 0.5 * (double)a.s->fprev[i]))
-      hn = 0.5 * (lo + hi);
-    a.s->fprev[i] = (float)fabs(f);
-    const double hcap = fmin(a.L[0], fmin(a.L[1], a.L[2])) / (3.0 * (1.0 + 1e-6));
-    if (hn > hcap) {
-      if (h >= hcap * (1.0 - 1e-12) && f < 0.0) atomicOr(&a.s->status, kErrBoxTooSmall);
-      hn = hcap;
-    }
-    if (fabs(hn - h) <= 5e-7 * h) {
-      conv = true;
-    } else {
-      a.s->h[i] = hn;
-      a.s->lo[i] = lo;
-      a.s->hi[i] = hi;
-      if (pass + 1 >= a.max_iter) atomicOr(&a.s->status, kErrNotConverged);
-      atomicAdd(&a.s->unconverged, 1);
-    }
+    a.s->h[i] = it.h;
+    a.s->lo[i] = it.lo;
+    a.s->hi[i] = it.hi;
+    a.s->fprev[i] = it.fprev;
+    if (pass + 1 >= a.max_iter) atomicOr(&a.s->status, kErrNotConverged);
+    atomicAdd(&a.s->unconverged, 1);
+    return;
   }
-  if (conv) {
-    const double h2 = h * h;
-    const double rho = 8.0 / 3.14159265358979323846 * (double)s.z / (h2 * h);
-    const double drho = -8.0 / 3.14159265358979323846 * (double)s.w / (h2 * h2);
-    const double omega = 1.0 + h / (3.0 * rho) * drho;
-    a.h_out[i] = h;
-    a.rho_out[i] = (float)rho;
-    a.omega_out[i] = (float)omega;
-    a.s->done[i] = 1;
-    if (!(rho > 0.0) || !(omega > 0.0)) atomicOr(&a.s->status, kErrNonPhysical);
-  }
+  const double h2 = h * h;
+  const double rho = 8.0 / 3.14159265358979323846 * (double)s.z / (h2 * h);
+  const double drho = -8.0 / 3.14159265358979323846 * (double)s.w / (h2 * h2);
+  const double omega = 1.0 + h / (3.0 * rho) * drho;
+  a.h_out[i] = h;
+  a.rho_out[i] = (float)rho;
+  a.omega_out[i] = (float)omega;
+  a.s->done[i] = 1;
+  if (!(rho > 0.0) || !(omega > 0.0)) atomicOr(&a.s->status, kErrNonPhysical);
 }
 
 __global__ void k_na_clear_counter(NaScratch *s) { s->unconverged = 0; }
@@ -214,7 +214,11 @@ extern "C" int sph_density_noalloc(int n, const double *box_len, const double *x
   cudaStream_t st = (cudaStream_t)cuda_stream;
   NaArgs a;
   a.n = n;
-  for (int d = 0; d < 3; ++d) a.L[d] = box_len[d];
+  for (int d = 0; d < 3; ++d) {
+    a.L[d] = box_len[d];
+    a.iL[d] = 1.0 / box_len[d];
+  }
+  a.hcap = std::fmin(box_len[0], std::fmin(box_len[1], box_len[2])) / (3.0 * (1.0 + 1e-6));
   a.x = x;
   a.m = m;
   a.n_ngb = n_ngb;
@@ -225,21 +229,27 @@ extern "C" int sph_density_noalloc(int n, const double *box_len, const double *x
   a.rho_out = rho_out;
   a.omega_out = omega_out;
   const int blocks = (n + kNaThreads - 1) / kNaThreads;
+  // each launch is checked as it is made, so an error reported here is one
+  // of this call's launches
   k_na_init<<<blocks, kNaThreads, 0, st>>>(a, h0);
-  int status = 0;
+  if (cudaGetLastError() != cudaSuccess) return SPH_ECUDA;
   for (int pass = 0; pass < max_iter; ++pass) {
     k_na_clear_counter<<<1, 1, 0, st>>>(a.s);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ECUDA;
     k_na_sums<<<blocks, kNaThreads, 0, st>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ECUDA;
     k_na_update<<<blocks, kNaThreads, 0, st>>>(a, pass);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ECUDA;
     int counters[2] = {0, 0};
     if (cudaMemcpyAsync(counters, &a.s->status, sizeof counters, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return SPH_ECUDA;
-    status = counters[0];
+    const int status = counters[0];
+    if (status & kErrInvalidInput) return SPH_EINVAL;
     if (status & kErrBoxTooSmall) return SPH_EBOXTOOSMALL;
     if (status & kErrNonPhysical) return SPH_ENONPHYSICAL;
-    if (counters[1] == 0) return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ECUDA;
+    if (counters[1] == 0) return SPH_OK;
   }
   return SPH_ENOTCONVERGED;
 }
