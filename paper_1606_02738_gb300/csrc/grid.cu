@@ -169,9 +169,14 @@ __device__ __forceinline__ unsigned warp_peers(int key, int &rank) {
 
 // Integer top-cell key and 30-bit Morton code (10 bits per axis inside the
 // top cell) of every particle, plus the cell histogram. The cell index is
-// floor(x / w) exactly (a product with 1/w, corrected by one step either way
-// in FP64), so rel = x - c w lies in [0, w). Histogram increments are
-// aggregated over the lanes of a warp that share a cell.
+// c = floor(x / w) exactly, for the FP64 values x and w: a product with 1/w,
+// corrected by one step either way where the sign of c w - x, taken from an
+// fma (the exact product and difference, rounded once, so its sign is the
+// exact sign), says the product was off. rel = x - c w (one fma, rounded
+// once) lies in [0, w), and each Morton coordinate is floor(rel (1024 / w))
+// with 1024 / w formed as (1 / w) x 1024 (exact power-of-two scaling).
+// Histogram increments are aggregated over the lanes of a warp that share a
+// cell.
 __global__ void k_cell_keys(GridArgs g) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = k < g.n;
@@ -183,15 +188,15 @@ __global__ void k_cell_keys(GridArgs g) {
     unsigned q[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      int c = (int)floor(x[d] * B.iw[d]);
-      if ((double)c * B.w[d] > x[d])
-        --c;
-      else if ((double)(c + 1) * B.w[d] <= x[d])
-        ++c;
+      int c = (int)floor(__dmul_rn(x[d], B.iw[d]));
+      if (fma((double)c, B.w[d], -x[d]) > 0.0)
+        --c;  // c w > x
+      else if (fma((double)(c + 1), B.w[d], -x[d]) <= 0.0)
+        ++c;  // (c + 1) w <= x
       c = c < 0 ? 0 : (c >= B.n[d] ? B.n[d] - 1 : c);
       ic[d] = c;
-      const double rel = x[d] - (double)c * B.w[d];
-      int qi = (int)floor(rel * (B.iw[d] * (double)(1 << kMaxDepth)));
+      const double rel = fma(-(double)c, B.w[d], x[d]);
+      int qi = (int)floor(__dmul_rn(rel, __dmul_rn(B.iw[d], (double)(1 << kMaxDepth))));
       qi = qi < 0 ? 0 : (qi > (1 << kMaxDepth) - 1 ? (1 << kMaxDepth) - 1 : qi);
       q[d] = (unsigned)qi;
     }
@@ -795,6 +800,41 @@ void launch_build_lists(const ListArgs &a, cudaStream_t s) {
   k_lists_warp<<<(a.n_targets + kLWarps - 1) / kLWarps, kLWarps * 32, 0, s>>>(a);
   note_launch();
   k_lists<<<(a.n_targets + 127) / 128, 128, 0, s>>>(a);  // flagged targets only
+  note_launch();
+}
+
+// ---------------------------------------------------------------- getters
+
+// Per particle (caller order): the integer coordinates of its top cell in its
+// box and the level of its octree leaf (out4[4 k ...]), and the leaf cell's
+// integer coordinates at that level inside the top cell (out3[3 k ...]).
+__global__ void k_get_cells(const int *orig, const int *leaf_of, const Leaf *leaves,
+                            const Node *nodes, const BoxDev *boxes, int n, int *out4,
+                            int *out3) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const Node nd = nodes[leaves[leaf_of[s]].node];
+  const BoxDev &B = boxes[nd.box];
+  int c[3];
+  cell_coords(B, nd.cell - B.cell_base, c);
+  const size_t k = (size_t)orig[s];
+  if (out4) {
+    out4[4 * k] = c[0];
+    out4[4 * k + 1] = c[1];
+    out4[4 * k + 2] = c[2];
+    out4[4 * k + 3] = nd.level;
+  }
+  if (out3) {
+    out3[3 * k] = nd.ix;
+    out3[3 * k + 1] = nd.iy;
+    out3[3 * k + 2] = nd.iz;
+  }
+}
+
+void launch_get_cells(const int *orig, const int *leaf_of, const Leaf *leaves, const Node *nodes,
+                      const BoxDev *boxes, int n, int *out4, int *out3, cudaStream_t s) {
+  if (n <= 0) return;
+  k_get_cells<<<(n + 255) / 256, 256, 0, s>>>(orig, leaf_of, leaves, nodes, boxes, n, out4, out3);
   note_launch();
 }
 

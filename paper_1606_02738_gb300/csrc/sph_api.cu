@@ -1396,9 +1396,29 @@ int sph_get(sph_ctx *c, int field, void *dev_out) {
     return fail(c, SPH_ESTATE, "field %d needs sph_density on the current positions", field);
   if (needs_force && !c->force_valid)
     return fail(c, SPH_ESTATE, "field %d needs sph_force on the current state", field);
+  if (field == SPH_CELL || field == SPH_LEAF_CELL) {
+    if (!c->grid_valid)
+      return fail(c, SPH_ESTATE, "field %d needs a grid of the current particles", field);
+    launch_get_cells(c->st.orig, c->leaf_of, as<Leaf>(c->leaves), as<Node>(c->nodes),
+                     c->boxes_d, c->n, field == SPH_CELL ? (int *)dev_out : nullptr,
+                     field == SPH_LEAF_CELL ? (int *)dev_out : nullptr, c->stream);
+    return sync_check(c);
+  }
   launch_get(field, dev_out, c->st.orig, c->n, c->st, c->rho, c->omega, c->P, c->nngb, c->niter,
              c->nforce, c->stream);
   return sync_check(c);
+}
+
+int sph_grid(const sph_ctx *c, int box, int32_t *n_out, double *w_out) {
+  if (!c) return SPH_EINVAL;
+  if (!c->loaded) return SPH_ESTATE;
+  if (box < 0 || box >= c->nb) return SPH_EINVAL;
+  const BoxDev &B = c->boxes_h[box];
+  for (int d = 0; d < 3; ++d) {
+    if (n_out) n_out[d] = B.n[d];
+    if (w_out) w_out[d] = B.w[d];
+  }
+  return SPH_OK;
 }
 
 int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_factor_out,

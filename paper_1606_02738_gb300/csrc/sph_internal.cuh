@@ -412,6 +412,10 @@ void launch_grid_check(const double *h, int n, const BoxDev *boxes, int nb,
                        cudaStream_t s);
 void launch_leaf_hmax(const GeomArgs &a, int n_nodes, cudaStream_t s);
 void launch_h_guess(const GeomArgs &a, double n_ngb, double *h, float *hf, cudaStream_t s);
+// Top-cell coordinates + leaf level ([N][4]) and leaf-cell coordinates
+// ([N][3]) per particle in caller order (either output may be null).
+void launch_get_cells(const int *orig, const int *leaf_of, const Leaf *leaves, const Node *nodes,
+                      const BoxDev *boxes, int n, int *out4, int *out3, cudaStream_t s);
 
 // ---- axis_sort.cu ----
 struct AxisSortArgs {

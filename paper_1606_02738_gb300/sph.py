@@ -25,7 +25,7 @@ ERROR_NAMES = {SPH_EINVAL: "SPH_EINVAL", SPH_ENOMEM: "SPH_ENOMEM", SPH_ECUDA: "S
                SPH_ESTATE: "SPH_ESTATE"}
 
 SPH_X, SPH_V, SPH_U, SPH_H, SPH_RHO, SPH_OMEGA, SPH_P, SPH_A, SPH_DUDT = range(9)
-SPH_NNGB, SPH_NITER, SPH_NFORCE, SPH_M = 9, 10, 11, 12
+SPH_NNGB, SPH_NITER, SPH_NFORCE, SPH_M, SPH_CELL, SPH_LEAF_CELL = 9, 10, 11, 12, 13, 14
 SPH_MODE_PLAIN, SPH_MODE_BATCHED = 0, 1
 SPH_PREC_FP32, SPH_PREC_KAHAN = 0, 1
 
@@ -34,10 +34,11 @@ FIELDS = {SPH_X: ("float64", 3), SPH_V: ("float32", 3), SPH_U: ("float32", 1),
           SPH_H: ("float64", 1), SPH_RHO: ("float32", 1), SPH_OMEGA: ("float32", 1),
           SPH_P: ("float32", 1), SPH_A: ("float32", 3), SPH_DUDT: ("float32", 1),
           SPH_NNGB: ("int32", 1), SPH_NITER: ("int32", 1), SPH_NFORCE: ("int32", 1),
-          SPH_M: ("float32", 1)}
+          SPH_M: ("float32", 1), SPH_CELL: ("int32", 4), SPH_LEAF_CELL: ("int32", 3)}
 FIELD_NAMES = {"x": SPH_X, "v": SPH_V, "u": SPH_U, "h": SPH_H, "rho": SPH_RHO,
                "omega": SPH_OMEGA, "P": SPH_P, "a": SPH_A, "dudt": SPH_DUDT,
-               "nngb": SPH_NNGB, "niter": SPH_NITER, "nforce": SPH_NFORCE, "m": SPH_M}
+               "nngb": SPH_NNGB, "niter": SPH_NITER, "nforce": SPH_NFORCE, "m": SPH_M,
+               "cell": SPH_CELL, "leaf_cell": SPH_LEAF_CELL}
 
 
 class sph_params(ctypes.Structure):
@@ -117,13 +118,14 @@ def lib(build_if_needed: bool = True):
         L.sph_autotune.argtypes = [P, P, P, P, P]
         L.sph_fp32_peak.argtypes = [I, P, P]
         L.sph_stats.argtypes = [P, ctypes.POINTER(sph_stats_t)]
+        L.sph_grid.argtypes = [P, I, P, P]
         L.sph_last_error.argtypes = [P]
         L.sph_last_error.restype = ctypes.c_char_p
         L.sph_destroy.argtypes = [P]
         L.sph_destroy.restype = None
         for f in ("sph_create", "sph_workspace_size", "sph_set_workspace", "sph_init",
                   "sph_density", "sph_force", "sph_step", "sph_get", "sph_get_pair_order",
-                  "sph_autotune", "sph_fp32_peak", "sph_stats"):
+                  "sph_autotune", "sph_fp32_peak", "sph_stats", "sph_grid"):
             getattr(L, f).restype = I
         _lib = L
         return L
@@ -248,6 +250,14 @@ def sph_stats(ctx) -> dict:
     return out
 
 
+def sph_grid(ctx, box: int = 0) -> dict:
+    """Top grid of one box as of the last regrid: cells per axis and FP64 widths."""
+    n = (ctypes.c_int32 * 3)()
+    w = (ctypes.c_double * 3)()
+    _check(ctx, lib().sph_grid(ctx, int(box), n, w), "sph_grid")
+    return {"n": list(n), "w": list(w)}
+
+
 def sph_last_error(ctx) -> str:
     return lib().sph_last_error(ctx).decode()
 
@@ -343,7 +353,7 @@ class Context:
     def get(self, name: str):
         f = FIELD_NAMES[name]
         dtype, comp = FIELDS[f]
-        shape = (self.n, 3) if comp == 3 else (self.n,)
+        shape = (self.n, comp) if comp > 1 else (self.n,)
         out = self.torch.empty(shape, dtype=getattr(self.torch, dtype), device=self.device)
         sph_get(self.ctx, f, out)
         return out
@@ -360,3 +370,6 @@ class Context:
 
     def stats(self) -> dict:
         return sph_stats(self.ctx)
+
+    def grid(self, box: int = 0) -> dict:
+        return sph_grid(self.ctx, box)
