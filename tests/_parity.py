@@ -2,14 +2,23 @@
 run the FP64 oracle on the same seeded inputs, compare with the stated
 tolerances (relative rho and h <= 1e-5; |a - a_ref| / max|a_ref| <= 1e-4,
 the same form for du/dt; neighbour counts exact except pairs within 1e-6 h of
-the kernel edge)."""
+the kernel edge, counted per particle).
+
+Omega's tolerance follows from h's: at fixed positions Omega = s / 3 with
+s = -(sum m q w') / (sum m w), so an error dh/h in h moves Omega by
+(d ln Omega / d ln h) dh/h. The GPU accepts h once |N - n_ngb| <= 1e-6 n_ngb
+(or its next step is below 5e-7 h), i.e. dh/h <= 1e-6 / (d ln N / d ln h)
+<= 2e-6 for the slopes these inputs have (>= 0.5), and |d ln Omega / d ln h|
+stays below 5 on them; with the FP32 rounding of the sums (~1e-6) that
+bounds the Omega error by ~1.1e-5, so the tests allow 2e-5."""
 import numpy as np
+from scipy.spatial import cKDTree
 
 import oracle
 
 TOL_RHO = 1e-5
 TOL_H = 1e-5
-TOL_OMEGA = 1e-4
+TOL_OMEGA = 2e-5
 TOL_A = 1e-4
 TOL_DU = 1e-4
 EDGE = 1e-6
@@ -37,15 +46,41 @@ def run_oracle(p, steps=0, dt=None):
     return s
 
 
+def _edge_density_box(x, box, h, eps):
+    t = cKDTree(x, boxsize=box)
+    up = t.query_ball_point(x, h * (1 + eps), return_length=True, workers=-1)
+    dn = t.query_ball_point(x, h * (1 - eps), return_length=True, workers=-1)
+    return t, np.asarray(up, dtype=np.int64) - np.asarray(dn, dtype=np.int64)
+
+
 def edge_pairs(s, factor=EDGE):
     """Per particle, the number of j whose distance lies within factor * h_i
-    of the kernel edge (where the integer counts may legitimately differ)."""
+    of the edge of i's kernel (where the density count may legitimately
+    differ), from the oracle's h."""
+    amb = np.zeros(s.x.shape[0], dtype=np.int64)
+    for b, sl in s.boxes():
+        _, amb[sl] = _edge_density_box(s.x[sl], s.box[b], s.h[sl], factor)
+    return amb
+
+
+def edge_pairs_force(s, factor=EDGE):
+    """Per particle, an upper bound of #{j : |r_ij - max(h_i, h_j)| <= factor
+    max(h_i, h_j)} (where the force count may legitimately differ): pairs on
+    the edge of i's own kernel plus those on the edge of j's."""
     amb = np.zeros(s.x.shape[0], dtype=np.int64)
     for b, sl in s.boxes():
         x, h = s.x[sl], s.h[sl]
-        up = oracle.neighbours(x, s.box[b], h * (1 + factor))
-        dn = oracle.neighbours(x, s.box[b], h * (1 - factor))
-        amb[sl] = np.array([len(a) - len(d) for a, d in zip(up, dn)])
+        t, own = _edge_density_box(x, s.box[b], h, factor)
+        amb[sl] += own
+        # j's kernel edge: the (rare) j whose shell holds some particle
+        up = t.query_ball_point(x, h * (1 + factor), return_length=True, workers=-1)
+        dn = t.query_ball_point(x, h * (1 - factor), return_length=True, workers=-1)
+        base = sl.start
+        for j in np.nonzero(np.asarray(up) > np.asarray(dn))[0]:
+            inner = set(t.query_ball_point(x[j], h[j] * (1 - factor)))
+            for i in t.query_ball_point(x[j], h[j] * (1 + factor)):
+                if i not in inner and i != j:
+                    amb[base + i] += 1
     return amb
 
 
@@ -82,8 +117,9 @@ def compare_force(g, s, tol_a=TOL_A, tol_du=TOL_DU):
     return err
 
 
-def force_counts_close(g, s, slack_frac=1e-4):
-    """Force-neighbour counts: equal except a tiny fraction of pairs on an
-    edge (|r - max(h_i, h_j)| below 1e-6 h)."""
+def force_counts_close(g, s):
+    """Force-neighbour counts #{j : r_ij < max(h_i, h_j)}: equal per particle
+    except pairs within 1e-6 max(h_i, h_j) of that edge."""
+    amb = edge_pairs_force(s)
     diff = np.abs(g["nforce"].astype(np.int64) - s.n_force)
-    assert diff.sum() <= max(2, slack_frac * s.n_force.sum()), (int(diff.sum()),)
+    assert np.all(diff <= amb), (int(diff.max()), int(np.sum(diff > amb)))
