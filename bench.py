@@ -2,12 +2,16 @@
 """Benchmark of the SPH hot path: neighbour interactions per second
 (density + force) on one GB300, and the fraction of the FP32 roofline.
 
-One step = one full kick-drift-kick step of the 3D Sod shock tube (972,000
-particles, periodic [0,2]x[0,0.25]^2): drift, cell grid (A1), octree split
-(A2), density with the smoothing-length iteration (A4, A5), force (A6) and
-the kicks (A7). The metric counts density interactions of the converged pass
-(ordered pairs j != i, r_ij < h_i) plus force interactions (r_ij <
-max(h_i, h_j)) and divides by the device time of the whole step.
+One step = one full kick-drift-kick step of the largest workload, 64M
+particles Poisson-sampled from a lognormal density field (sigma_lnrho = 1.5,
+P(k) ~ k^-2 on 256^3, periodic unit box): drift, cell grid (A1: a regrid,
+or on a grid still valid for the drifted particles a refresh of positions
+and boxes), octree split (A2), density with the smoothing-length iteration
+(A4, A5), force (A6) and the kicks (A7). The metric counts density
+interactions of the converged pass (ordered pairs j != i, r_ij < h_i) plus
+force interactions (r_ij < max(h_i, h_j)) and divides by the device time of
+the whole step. `--workload` selects another configuration; by default the
+line also carries a summary of the other four (both interaction forms).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -59,8 +63,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload's particle count (same recipe) for profiling")
-    ap.add_argument("--workload", default="sod", choices=["sod", "uniform", "clustered",
-                                                          "batched", "lognormal"])
+    ap.add_argument("--workload", default="lognormal", choices=["sod", "uniform", "clustered",
+                                                                "batched", "lognormal"])
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the summary of the other configurations (both forms)")
+    ap.add_argument("--config-steps", type=int, default=8,
+                    help="timed steps per form in the summary of the other configurations")
     return ap.parse_args()
 
 
@@ -290,7 +298,97 @@ def time_per_box(p, dt, args, dev, stream, flush, tuned, sph, torch):
             "kernel_launches_per_step": launches / args.steps}
 
 
+def kernel_roofline(s0, s1, inter_d, inter_f, ms, peak):
+    """Achieved FP32 rate of the density and force kernels from the library's
+    CUDA events (algorithmic flops of the counted interactions / kernel time)."""
+    kern = {}
+    for name, flops, t_key, n_key, ikey in (
+            ("density", FLOPS_DENSITY, "t_density_ms", "density_launches", inter_d),
+            ("force", FLOPS_FORCE, "t_force_ms", "force_launches", inter_f)):
+        t = s1[t_key] - s0[t_key]
+        n = max(1, s1[n_key] - s0[n_key])
+        achieved = flops * ikey / (t / 1000.0) / 1e12 if t > 0 else 0.0
+        kern[name] = {"achieved": achieved, "frac": achieved / peak, "launches": n,
+                      "ms_per_launch": t / n, "share_of_step": t / ms if ms > 0 else 0.0,
+                      "flops_per_launch": flops * ikey / n}
+    return kern
+
+
+def step_kinds(s0, s1):
+    """Steps of the timed region by kind: on the reused grid (of those, redone on
+    a new grid, and launched as one CUDA graph), and with a regrid."""
+    return {k: int(s1[k] - s0[k]) for k in ("reused_steps", "redone_steps", "graph_steps")}
+
+
+def time_form(p, dt, mode, steps, warmup, dev, stream, flush, sph, torch, peak,
+              pair_sort=True):
+    """One interaction form on one workload with the bench's protocol: load,
+    density + force, the library's autotuner (untimed), `warmup` steps, then
+    `steps` KDK steps timed one by one with CUDA events, L2 flushed between.
+    Returns the rate, ms per step, kernel rooflines and step kinds."""
+    c = sph.Context(mode=mode, profile=True, pair_sort=pair_sort, device=dev)
+    c.load(p)
+    c.density()
+    c.force()
+    tuned = c.autotune()
+    if dt is None:
+        dt = cfl_dt(c, p.gamma)
+    for _ in range(warmup):
+        c.step(dt, 1)
+    torch.cuda.synchronize(dev)
+    s0 = c.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        c.step(dt, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    s1 = c.stats()
+    c.close()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    inter_d = s1["total_density_interactions"] - s0["total_density_interactions"]
+    inter_f = s1["total_force_interactions"] - s0["total_force_interactions"]
+    kern = kernel_roofline(s0, s1, inter_d, inter_f, ms, peak)
+    return {"mode": "plain" if mode == sph.SPH_MODE_PLAIN else "batched", "autotune": tuned,
+            "dt": dt, "value": (inter_d + inter_f) / (ms / 1000.0), "ms_per_step": ms / steps,
+            "interactions_per_step": (inter_d + inter_f) / steps,
+            "density_frac": kern["density"]["frac"], "force_frac": kern["force"]["frac"],
+            "kernels": kern, "steps": step_kinds(s0, s1)}
+
+
+def config_summary(headline, args, dev, stream, flush, sph, torch, peak):
+    """The other configurations, both interaction forms, with the bench's
+    protocol (fewer steps): rate, ms per step, batched / per-pass ratio and the
+    FP32 fractions of the interaction kernels."""
+    out = {}
+    for name in ("uniform", "sod", "clustered", "batched", "lognormal"):
+        if name == headline:
+            continue
+        p, dt, wname = workload(name, args.scale)
+        rec = {"n_particles": p.n}
+        for mode in (sph.SPH_MODE_BATCHED, sph.SPH_MODE_PLAIN):
+            r = time_form(p, dt, mode, args.config_steps, 3, dev, stream, flush, sph, torch,
+                          peak)
+            rec[r["mode"]] = {k: r[k] for k in ("value", "ms_per_step", "density_frac",
+                                                "force_frac", "autotune", "steps")}
+        rec["batched_over_plain"] = rec["batched"]["value"] / rec["plain"]["value"]
+        out[wname] = rec
+        del p
+    return out
+
+
 # ------------------------------------------------------------ CPU oracle
+
+def step_label(kinds, steps):
+    """What the timed steps were, from the library's step counters."""
+    reg = steps - kinds["reused_steps"]
+    return (f"kick-drift-kick steps: {reg} with a regrid, {kinds['reused_steps']} on the "
+            f"previous grid (positions and boxes refreshed; {kinds['graph_steps']} of them "
+            f"one CUDA graph launch, {kinds['redone_steps']} redone on a new grid); each: "
+            f"density with the h iteration, force, kicks")
+
 
 def cpu_baseline(p, min_s: float = 10.0, max_reps: int = 20, note: str = "") -> dict:
     """The FP64 oracle, as it stands, on h-iterated density + force
@@ -456,16 +554,8 @@ def run_ours(args, d: Dist):
     # recorded by the library on this stream)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak, peak_src = fp32_peak_tflops(sm_count)
-    kern = {}
-    for name, flops, t_key, n_key, ikey in (
-            ("density", FLOPS_DENSITY, "t_density_ms", "density_launches", inter_d),
-            ("force", FLOPS_FORCE, "t_force_ms", "force_launches", inter_f)):
-        t = s1[t_key] - s0[t_key]
-        n = max(1, s1[n_key] - s0[n_key])
-        achieved = flops * ikey / (t / 1000.0) / 1e12 if t > 0 else 0.0
-        kern[name] = {"achieved": achieved, "launches": n, "ms_per_launch": t / n,
-                      "share_of_step": t / ms if ms > 0 else 0.0,
-                      "flops_per_launch": flops * ikey / n}
+    kern = kernel_roofline(s0, s1, inter_d, inter_f, ms, peak)
+    kinds = step_kinds(s0, s1)
     dom = max(kern, key=lambda k: kern[k]["share_of_step"])
     roof = {"bound": "alu", "achieved": kern[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
             "frac": kern[dom]["achieved"] / peak, "traffic": kernel_traffic(dom, args.mode, wname),
@@ -534,37 +624,18 @@ def run_ours(args, d: Dist):
     other = None
     if not args.no_compare:
         omode = sph.SPH_MODE_PLAIN if mode == sph.SPH_MODE_BATCHED else sph.SPH_MODE_BATCHED
-        oc = sph.Context(mode=omode, profile=True, pair_sort=not args.no_pair_sort, device=dev)
-        oc.load(p)
-        oc.density()
-        oc.force()
-        otuned = None if args.no_autotune else oc.autotune()
-        for _ in range(args.warmup):
-            oc.step(dt, 1)
-        torch.cuda.synchronize(dev)
-        o0 = oc.stats()
-        oev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            oev[k][0].record(stream)
-            oc.step(dt, 1)
-            oev[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-        o1 = oc.stats()
-        oms = sum(a.elapsed_time(b) for a, b in oev)
-        ointer = (o1["total_density_interactions"] - o0["total_density_interactions"] +
-                  o1["total_force_interactions"] - o0["total_force_interactions"])
-        other = {"mode": "plain" if omode == sph.SPH_MODE_PLAIN else "batched",
-                 "autotune": otuned,
-                 "value": ointer / (oms / 1000.0), "ms_per_step": oms / args.steps,
-                 "interactions_per_step": ointer / args.steps}
-        oc.close()
+        other = time_form(p, dt, omode, args.steps, args.warmup, dev, stream, flush, sph, torch,
+                          peak, pair_sort=not args.no_pair_sort)
+        other.pop("kernels", None)
 
     # config 4: the same boxes as one context each (one launch sequence per box)
     per_box = None
     if p.n_boxes > 1 and not args.no_compare:
         per_box = time_per_box(p, dt, args, dev, stream, flush, tuned, sph, torch)
+
+    configs = None
+    if not args.no_configs and not args.no_compare:
+        configs = config_summary(args.workload, args, dev, stream, flush, sph, torch, peak)
 
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
@@ -578,8 +649,10 @@ def run_ours(args, d: Dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": wname, "n_particles": p.n, "dt": dt,
-                       "step": "one kick-drift-kick step: regrid, density (h iteration), "
-                               "force, kicks",
+                       "step": step_label(kinds, args.steps),
+                       "reused_steps": kinds["reused_steps"],
+                       "redone_steps": kinds["redone_steps"],
+                       "graph_steps": kinds["graph_steps"],
                        "mode": args.mode, "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": "replicas" if d.world > 1 else "single GPU",
                        "interactions_per_step": inter / args.steps,
@@ -607,6 +680,7 @@ def run_ours(args, d: Dist):
             "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
             "other_form": other,
             "per_box_launches": per_box,
+            "configs": configs,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

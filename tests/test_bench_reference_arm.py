@@ -27,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
               "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["steps"] == 1 and d["warmup"] == 1 and d["config"]["workload"] == "sod3d_972k"
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["config"]["workload"] == "lognormal_64M"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert cb["unit"] == d["unit"] and "subset" in cb["sample"]
