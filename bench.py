@@ -544,6 +544,9 @@ def run_ours(args, d: Dist):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     s1 = ctx.stats()
+    # density passes each particle needed in the last timed step (histogram)
+    niter = torch.bincount(ctx.get("niter").long().clamp(0, 31)).cpu().tolist()
+    passes_hist = {str(k): v / p.n for k, v in enumerate(niter) if v}
     ms = sum(a.elapsed_time(b) for a, b in ev)
     inter_d = s1["total_density_interactions"] - s0["total_density_interactions"]
     inter_f = s1["total_force_interactions"] - s0["total_force_interactions"]
@@ -667,6 +670,12 @@ def run_ours(args, d: Dist):
                        "stage_max": [s1["stage_max_density"], s1["stage_max_force"]],
                        "direct_warps_last_step": [s1["direct_list_warps"],
                                                   s1["direct_stage_warps"]],
+                       "density_passes_hist_last_step": passes_hist,
+                       "neighbour_cache_last_step": {
+                           "groups": s1["n_groups"],
+                           "density_on_cache": s1["cache_density_groups"],
+                           "force_on_cache": s1["cache_force_groups"],
+                           "built": s1["cache_built_groups"]},
                        "pair_sort": not args.no_pair_sort,
                        "autotune": tuned,
                        "leaves": s1["n_leaves"]},

@@ -89,7 +89,9 @@ typedef struct sph_ctx sph_ctx; /* opaque, owned by the library */
 typedef struct {
   double gamma;    /* adiabatic index (P = (gamma - 1) rho u) */
   double n_ngb;    /* target weighted neighbour number (> 32/3) */
-  double h_tol;    /* converged when |N_i - n_ngb| <= h_tol * n_ngb */
+  double h_tol;    /* converged when |N_i - n_ngb| <= h_tol * n_ngb and, to first order, h_i
+                      lies within 5e-7 h_i of the root (|N_i - n_ngb| <= 5e-7 N_i d ln N/d ln h),
+                      or the next step would move h_i by <= 5e-7 h_i */
   int max_iter;    /* density passes before SPH_ENOTCONVERGED */
   int n_split;     /* split octree cells holding more particles than this (8..256) */
   int precision;   /* SPH_PREC_* */
@@ -109,6 +111,13 @@ typedef struct {
                       (fewer groups to the second tier on clumped inputs) */
   double cell_factor; /* top-cell edge >= cell_factor x the largest h where the box allows
                          (1 <= cell_factor <= 4; >= 1 x always) */
+  int reuse_lists;  /* batched form, 1: keep each group's staged neighbours and per-lane
+                       neighbour lists in device memory after the density; the force of the
+                       same call takes its pairs from them (plus the pairs reached by a
+                       neighbour's larger h), and later density calls reuse them while a
+                       bound on the distance moved since they were built (the summed |v dt|
+                       of the drifts) shows them complete for the current h; 0: search
+                       anew in every call (same results up to summation order) */
 } sph_params;
 
 typedef struct {
@@ -172,11 +181,16 @@ typedef struct {
   int64_t redone_steps;       /* of those, steps redone on a new grid because a particle had
                                  moved too far from its top cell (cumulative) */
   int64_t graph_steps;        /* of those, steps launched as one CUDA graph (cumulative) */
+  /* Neighbour cache (reuse_lists = 1), batched form, last density / force: */
+  int64_t n_groups;           /* target groups (<= 32 consecutive particles of a top cell) */
+  int64_t cache_density_groups; /* groups whose density ran on their stored neighbours */
+  int64_t cache_force_groups;   /* groups whose force ran on the density's neighbours */
+  int64_t cache_built_groups;   /* groups whose density searched anew and stored them */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,
  * n_split = 64, FP32, batched mode, pair sorts on, grid reuse on, profiling
- * off, tile 0, cell_factor 2. */
+ * off, tile 0, cell_factor 2, list reuse on. */
 void sph_default_params(sph_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a

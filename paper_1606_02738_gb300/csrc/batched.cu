@@ -235,18 +235,100 @@ void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s) {
 constexpr int kWalkWarps = 4;
 constexpr int kFront = 512;
 
-template <bool TIGHT>
-__global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(GroupListArgs a) {
+// Walk modes: the plain walk of every group (with the neighbour cache: only
+// the groups that need one), the tight walk of the groups it queued, and the
+// far-reacher walk of the force (below).
+enum { kWalkPlain = 0, kWalkTight = 1, kWalkFar = 2 };
+
+// Largest over the lanes of a warp.
+__device__ __forceinline__ float warp_max_f(float v) {
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// delta of the neighbour cache: the largest path length since the epoch
+// began over the particles of the 27 top cells around `cell` (every lane of
+// the warp gets it; lanes 0..26 read one cell each).
+__device__ __forceinline__ float cell_motion(const CacheArgs &C, const BoxDev &B, int cell,
+                                             int lane) {
+  int c[3];
+  cell_xyz(B, cell - B.cell_base, c);
+  float m = 0.f;
+  if (lane < 27) {
+    const int dx = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dz = lane % 3 - 1;
+    const int nc = B.cell_base + (((c[0] + dx + B.n[0]) % B.n[0]) * B.n[1] +
+                                  (c[1] + dy + B.n[1]) % B.n[1]) * B.n[2] +
+                   (c[2] + dz + B.n[2]) % B.n[2];
+    m = __uint_as_float(C.dmax_cell[nc]);
+  }
+  return warp_max_f(m);
+}
+
+// Far-reacher walk (force, neighbour cache): a group whose density finished
+// in the first tier on per-lane lists can take its force pairs from the
+// stored stage and lists, unless some particle outside the stage has an h
+// that reaches the group. Outside the stage means at distance >= Reff =
+// Rg - max_i dpath_i - delta from every target now, so only nodes whose
+// largest h exceeds Reff and that lie within that h of the group box can
+// hold one: the walk follows only those and stops at the first leaf.
+// fuse[g] = 1 when none exists.
+template <int MODE>
+__global__ void __launch_bounds__(kWalkWarps * 32, MODE == kWalkTight ? 4 : 10)
+    k_group_walk(GroupListArgs a) {
   __shared__ int front_all[kWalkWarps][2][kFront];  // node << 5 | neighbour code (0..26)
-  constexpr bool tight = TIGHT;
+  constexpr bool tight = MODE == kWalkTight;
+  constexpr bool far = MODE == kWalkFar;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ltmask = (1u << lane) - 1u;
   const int ng = tight ? *a.walk_queued : a.n_groups;
+  int n_reused = 0, n_failed = 0;
   for (int q = blockIdx.x * kWalkWarps + warp; q < ng; q += gridDim.x * kWalkWarps) {
     const int g = tight ? a.walk_queue[q] : q;
     int *cur = front_all[warp][0], *nxt = front_all[warp][1];
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
+    float far_thr = 0.f;  // far walk: the effective stage radius Reff
+    if (MODE == kWalkPlain && a.cache_on && !a.force) {
+      // density: is the stored stage still complete for the starting h?
+      bool reuse = false;
+      const GroupCache &M = a.cache.meta[g];
+      if (!a.cache.ctl->build_all && M.stage_ok) {
+        float hm = 0.f, need = 0.f;
+        if (lane < G.count) {
+          hm = a.hf[G.start + lane];
+          need = hm + a.cache.dpath[G.start + lane];
+        }
+        hm = warp_max_f(hm);
+        need = warp_max_f(need) + cell_motion(a.cache, B, G.cell, lane);
+        reuse = need <= M.Rg;
+        // failures caused by motion count toward a new epoch (one that resets
+        // the path lengths); an h that outgrew the stage rebuilds regardless
+        if (!reuse && hm <= M.Rg) ++n_failed;
+      }
+      if (lane == 0) a.cache.gmode[g] = reuse ? 1 : 0;
+      if (reuse) {
+        ++n_reused;
+        continue;  // the stored task slots and count stay
+      }
+    }
+    if (MODE == kWalkPlain && a.cache_on && a.force && a.cache.fuse[g]) {
+      if (lane == 0) a.count[g] = 0;  // the force reuses the density's cache: no walk
+      continue;
+    }
+    if (far) {
+      // candidates: every warp of the group finished its density on lists
+      const GroupCache &M = a.cache.meta[g];
+      bool ok = true;
+      for (int w = 0; w < 4; ++w)
+        if (w * 8 < G.count && !M.wok[w]) ok = false;
+      if (!ok) {
+        if (lane == 0) a.cache.fuse[g] = 0;
+        continue;
+      }
+      float dt = lane < G.count ? a.cache.dpath[G.start + lane] : 0.f;
+      dt = warp_max_f(dt);
+      far_thr = M.Rg - dt - cell_motion(a.cache, B, G.cell, lane);
+    }
     int c[3];
     cell_xyz(B, G.cell - B.cell_base, c);
     const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
@@ -309,7 +391,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(
           }
         }
         bool pass = false;
-        if (!tight) {
+        if (far) {
+          float d2 = 0.f;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float gap = fmaxf(0.f, fmaxf(lo[d] - G.thi[d], G.tlo[d] - hi[d]));
+            d2 = fmaf(gap, gap, d2);
+          }
+          const float crit = shm + B.eps;
+          pass = valid && shm > far_thr && d2 < crit * crit;
+        } else if (!tight) {
           float d2 = 0.f;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
@@ -334,7 +425,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(
         }
         const bool leaf_in = pass && child < 0, inner_in = pass && child >= 0;
         const unsigned ml = __ballot_sync(0xffffffffu, leaf_in);
-        if (leaf_in) {
+        if (far) {  // a far reacher exists: stop (no tasks are written)
+          if (ml) {
+            ntask = 1;
+            nn = 0;
+            break;
+          }
+        } else if (leaf_in) {
           const int pos = ntask + __popc(ml & ltmask);
           if (pos < a.tcap) {
             const int dx = code / 9 - 1, dy = (code / 3) % 3 - 1, dz = code % 3 - 1;
@@ -357,6 +454,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(
         nn += 8 * __popc(mi);
       }
       __syncwarp();
+      if (far && ntask) break;
       if (nn > kFront) {
         overflow = true;
         break;
@@ -367,11 +465,24 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(
       n = nn;
     }
     __syncwarp();  // the frontier buffers are reused by this warp's next group
+    if (far) {  // a frontier overflow counts as a far reacher (full path)
+      if (lane == 0) a.cache.fuse[g] = (ntask == 0 && !overflow) ? 1 : 0;
+      if (ntask == 0 && !overflow) ++n_reused;
+      continue;
+    }
     overflow = overflow || ntask > a.tcap;
     if (lane == 0) {
       a.count[g] = overflow ? a.tcap + 1 : ntask;
       if (overflow && !tight && a.walk_queue) a.walk_queue[atomicAdd(a.walk_queued, 1)] = g;
+      if (a.wmode) a.wmode[g] = tight ? 1 : 0;
     }
+  }
+  if (a.cache_on && lane == 0 && (n_reused || n_failed)) {
+    if (MODE == kWalkPlain && !a.force) {
+      atomicAdd(&a.ctr->cache_used[0], n_reused);
+      if (n_failed) atomicAdd(&a.cache.ctl->fail, n_failed);
+    }
+    if (far) atomicAdd(&a.ctr->cache_used[1], n_reused);
   }
 }
 
@@ -380,12 +491,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TIGHT ? 4 : 10) k_group_walk(
 // device).
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
-  k_group_walk<false><<<(a.n_groups + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0, s>>>(a);
+  const int gblocks = (a.n_groups + kWalkWarps - 1) / kWalkWarps;
+  if (a.cache_on && a.force) {  // far reachers decide which groups reuse the cache
+    k_group_walk<kWalkFar><<<gblocks, kWalkWarps * 32, 0, s>>>(a);
+    note_launch();
+  }
+  k_group_walk<kWalkPlain><<<gblocks, kWalkWarps * 32, 0, s>>>(a);
   note_launch();
   if (!a.walk_queue) return;
-  const int blocks = a.n_groups < 152 * 8 * kWalkWarps ? (a.n_groups + kWalkWarps - 1) / kWalkWarps
-                                                       : 152 * 8;
-  k_group_walk<true><<<blocks, kWalkWarps * 32, 0, s>>>(a);
+  const int blocks = a.n_groups < 152 * 8 * kWalkWarps ? gblocks : 152 * 8;
+  k_group_walk<kWalkTight><<<blocks, kWalkWarps * 32, 0, s>>>(a);
   note_launch();
 }
 
@@ -434,6 +549,8 @@ constexpr float kFar = 1e18f;
 
 template <int NS>
 struct DensSmem {
+  unsigned dmax_bits;                       // largest dpath of a reloaded stage (float bits)
+  unsigned pad_[3];
   float4 tgt[32];                           // tight stage: target position (group frame), radius
   float4 stage[NS + 1];                     // position in the group frame, m; [NS] sentinel
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
@@ -469,6 +586,7 @@ __device__ __forceinline__ int tier_count(int tier, int n_groups, const int *que
 struct StageRange {
   int total;      // staged entries, all warps
   int over;       // some warp's share outgrew its segment (the stage is incomplete)
+  int unmapped;   // (stored stage) some batch of tasks had no task map: slots not stored
   int maxw;       // largest warp share
   int segcap;     // entries per segment
   int pre1, pre2, pre3;  // prefix counts of segments 0, 0..1, 0..2
@@ -480,7 +598,8 @@ struct StageRange {
 };
 
 constexpr int kMap = 1024;  // per-warp particle -> task map (bytes, aliases the warp's cand)
-static_assert(kCandD * 2 >= kMap && kCandF * 2 >= kMap && kCandFL * 2 >= kMap,
+constexpr int kMapD = 2048; // the density's (its cand is larger)
+static_assert(kCandD * 2 >= kMapD && kCandF * 2 >= kMap && kCandFL * 2 >= kMap,
               "task map must fit a warp's cand");
 static_assert(kStageD % kNW == 0 && kStageF % kNW == 0 && kBigStageD % kNW == 0 &&
                   kBigStageF % kNW == 0 && kStageDL % kNW == 0 && kStageFL % kNW == 0,
@@ -495,11 +614,14 @@ static_assert(kStageD % kNW == 0 && kStageF % kNW == 0 && kBigStageD % kNW == 0 
 // particle's task from the map and the task's base and shift by shuffles.
 // Passing particles are appended to the warp's segment by ballot. Called by
 // every thread of the block.
+// st_j / st_slot (density, first tier, neighbour cache): each staged
+// particle's index and task slot are also written there, at its stage slot.
 template <bool FORCE>
 __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs *fa,
                                   const Group &G, int e0, int e1, int warp, int lane, float Rg,
                                   float4 *sq, float2 *sf, int *sj, int *wcount,
-                                  unsigned char *tmap, int cap, const float4 *tgt) {
+                                  unsigned char *tmap, int cap, const float4 *tgt,
+                                  int *st_j = nullptr, unsigned short *st_slot = nullptr) {
   const unsigned ltmask = (1u << lane) - 1u;
   const Task *tasks = FORCE ? fa->tasks : da->tasks;
   const Leaf *leaves = FORCE ? fa->leaves : da->leaves;
@@ -507,8 +629,10 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   const int ntask = e1 - e0;
   const int segcap = cap / kNW;
   const int base = warp * segcap;
+  constexpr int map_cap = FORCE ? kMap : kMapD;
   __syncthreads();  // every warp is done with the previous group's stage
   int nst = 0;
+  bool unmapped = false;
   for (int tb = warp; tb < ntask; tb += 32 * kNW) {
     const int mt = tb + lane * kNW;  // this lane's task
     int start = 0, cnt = 0;
@@ -530,7 +654,8 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int jbase = start - (incl - cnt);  // particle of flat index f: jbase_t + f
-    const bool mapped = total <= kMap;       // warp-uniform
+    const bool mapped = total <= map_cap;    // warp-uniform
+    unmapped |= !mapped;
     if (mapped) {
       for (int f = incl - cnt; f < incl; ++f) tmap[f] = (unsigned char)lane;
       __syncwarp();
@@ -596,6 +721,11 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
             sf[base + pos] = make_float2(fj[u].z, fj[u].w);
             sj[base + pos] = jj[u];
           }
+          if (st_j) {  // the task of flat index f: from the map (else not stored)
+            st_j[base + pos] = jj[u];
+            const int tl = mapped ? (int)tmap[f0 + 32 * u + lane] : 0;
+            st_slot[base + pos] = (unsigned short)(tb + tl * kNW);
+          }
         }
         nst += __popc(m);
       }
@@ -613,6 +743,7 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   r.total = r.pre3 + c3;
   r.maxw = max(max(c0, c1), max(c2, c3));
   r.over = r.maxw > segcap;
+  r.unmapped = __syncthreads_or(unmapped);
   return r;
 }
 
@@ -737,7 +868,61 @@ struct DensAcc {
   }
 };
 
-template <bool KAHAN, int NS>
+// Reload a group's stored stage (neighbour cache) into shared memory at the
+// current positions: entry k of segment w (k < wc[w]) is particle sj[k],
+// moved into the group frame by its task's shift (the same sum as the
+// staging, so the same FP32 values). FORCE also stages (A', h^2) and the
+// index. Returns the stage range; *dmax receives the largest dpath of the
+// staged particles. Called by every thread of the block.
+template <bool FORCE>
+__device__ StageRange load_stage_cached(const CacheArgs &C, int g, const int wc[4],
+                                        const Task *tasks, const float4 *pm, const float4 *fi,
+                                        float4 *sq, float2 *sf, int *sj, int cap,
+                                        unsigned *dmax_bits, float *dmax) {
+  __syncthreads();  // every warp is done with the previous group's stage
+  StageRange r;
+  r.segcap = cap / kNW;
+  r.pre1 = wc[0];
+  r.pre2 = wc[0] + wc[1];
+  r.pre3 = r.pre2 + wc[2];
+  r.total = r.pre3 + wc[3];
+  r.maxw = max(max(wc[0], wc[1]), max(wc[2], wc[3]));
+  r.over = 0;
+  r.unmapped = 0;
+  if (threadIdx.x == 0) *dmax_bits = 0u;
+  const size_t base = (size_t)g * C.ns;
+  float dm = 0.f;
+  __syncthreads();
+  for (int t = threadIdx.x; t < r.total; t += blockDim.x) {
+    const int k = r.index(t);
+    const int j = C.sj[base + k];
+    const Task tk = tasks[C.slot[base + k]];
+    const float4 p4 = pm[j];
+    float4 q = make_float4(tk.sx, tk.sy, tk.sz, 0.f);
+    q.x += p4.x;
+    q.y += p4.y;
+    q.z += p4.z;
+    q.w = p4.w;
+    sq[k] = q;
+    if (FORCE) {
+      const float4 f = fi[j];
+      sf[k] = make_float2(f.z, f.w);
+      sj[k] = j;
+    }
+    dm = fmaxf(dm, C.dpath[j]);
+  }
+  dm = warp_max_f(dm);
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits, __float_as_uint(dm));
+  __syncthreads();
+  *dmax = __uint_as_float(*dmax_bits);
+  return r;
+}
+
+// REUSE (first tier, neighbour cache): this instantiation runs the groups
+// whose stored stage is still valid (gmode[g] = 1) from that stage; the other
+// runs the rest, staging anew and storing the stage and lists. Two
+// instantiations keep each path's registers apart.
+template <bool KAHAN, int NS, bool REUSE>
 __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -751,8 +936,10 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0};
+  int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0}, n_built = 0;
   if (threadIdx.x == 0) S.stage[NS] = make_float4(kFar, kFar, kFar, 0.f);  // read after a barrier
+  // the neighbour cache: first tier only
+  const bool use_cache = !TIGHT && a.cache_on;
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
@@ -762,8 +949,15 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
     const float hcap = (float)B.hcap;
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
+    if (use_cache && (a.cache.gmode[g] != 0) != REUSE) continue;  // the other instantiation's
+    // tasks from the tight walk: complete only within each target's own
+    // starting radius (block-uniform; a reused stage never came from one)
+    const bool tightw = !REUSE && !TIGHT && a.wmode && a.wmode[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
+    constexpr bool reuse = REUSE;
+    GroupCache *M = use_cache ? &a.cache.meta[g] : nullptr;
+    float Rgb = Rg, Dst = 0.f;   // stage radius at the build, largest staged dpath
     if (TIGHT) __syncthreads();  // the previous group's warps are done reading tgt
     if (TIGHT && threadIdx.x < 32) {  // tight stage: each target's own radius
       float4 t = make_float4(0.f, 0.f, 0.f, -1.f);
@@ -774,12 +968,29 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
       }
       S.tgt[threadIdx.x] = t;  // read after stage_group's opening barrier
     }
-    const StageRange sr =
-        stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane, Rg, S.stage,
-                           nullptr, nullptr, S.wcount, (unsigned char *)cand, NS,
-                           TIGHT ? S.tgt : nullptr);
+    StageRange sr;
+    if constexpr (REUSE) {
+      int wc[4];
+      for (int w = 0; w < 4; ++w) wc[w] = M->wc[w];
+      Rgb = M->Rg;
+      sr = load_stage_cached<false>(a.cache, g, wc, a.tasks + e0, a.pm, nullptr, S.stage,
+                                    nullptr, nullptr, NS, &S.dmax_bits, &Dst);
+    } else {
+      sr = stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane, Rg, S.stage,
+                              nullptr, nullptr, S.wcount, (unsigned char *)cand, NS,
+                              TIGHT ? S.tgt : nullptr,
+                              use_cache ? a.cache.sj + (size_t)g * a.cache.ns : nullptr,
+                              use_cache ? a.cache.slot + (size_t)g * a.cache.ns : nullptr);
+      if (use_cache && threadIdx.x == 0) {
+        for (int w = 0; w < 4; ++w) M->wc[w] = min(S.wcount[w], sr.segcap);
+        M->Rg = Rg;
+        M->stage_ok = !sr.over && nt <= a.tcap && !sr.unmapped && !tightw;
+        ++n_built;
+      }
+    }
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
+      if (use_cache && threadIdx.x < kNW) M->wok[threadIdx.x] = 0;
       if (threadIdx.x < kNW && (TIGHT || nt > a.tcap))  // the third tier walks its targets
         a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + threadIdx.x;
       else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap)  // second tier: tight stage
@@ -793,13 +1004,18 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     float px = 0.f, py = 0.f, pz = 0.f;
     HIterF it;
     it.start(has ? a.hf[i] : 1.f);
+    // with tasks from the tight walk, this target's own walked radius
+    const float Rtight = fminf(it.h * a.skin_stage, wmin);
     if (has) {
       const float4 q = a.gpos[i];
       px = q.x;
       py = q.y;
       pz = q.z;
     }
-    if (!__any_sync(0xffffffffu, has)) continue;  // this warp has no targets
+    if (!__any_sync(0xffffffffu, has)) {  // this warp has no targets
+      if (use_cache && lane == 0) M->wok[warp] = 1;
+      continue;
+    }
     float blo[3], bhi[3];
     sub_box(has, px, py, pz, blo, bhi);
 
@@ -808,17 +1024,46 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     // candidates directly; 2: the candidates outgrew kCandD, the warp reads
     // the whole stage (slower, same sums)
     int mode = 0;
-    int ncand = 0, cnt = 0, passes = 0, ngb = 0;
+    int ncand = 0, cnt = 0, passes = 0, ngb = 0, tpad = 0;
     float rsub = 0.f, rl = 0.f;
+    // radius within which the stage is complete for this warp's targets: Rg
+    // when staged now; with a reused stage, Rg - dpath_i - delta (minimum over
+    // the warp)
+    float Rgw = Rg;
+    bool fresh = true;      // the per-lane lists were built in this call
+    bool have_cand = true;  // cand holds the filtered stage (else a list rebuild refilters)
+    if constexpr (REUSE) {
+      const size_t lrow = ((size_t)g * kNW + warp) * a.cache.lane_cap * 32;
+      const float dp = has ? a.cache.dpath[i] : 0.f;
+      const float delta = cell_motion(a.cache, B, G.cell, lane);
+      float rw = has ? Rgb - dp - delta : 3e38f;
+      for (int o = 16; o; o >>= 1) rw = fminf(rw, __shfl_xor_sync(0xffffffffu, rw, o));
+      Rgw = rw;
+      const int tp = M->tpad[warp];
+      if (tp >= 0) {  // stored lists: complete within rl_i - dpath_i - D for staged j
+        for (int t = 0; t < tp; ++t) list[t * 32 + lane] = a.cache.list[lrow + t * 32 + lane];
+        __syncwarp();
+        cnt = tp;
+        tpad = tp;
+        rl = has ? a.cache.rl[i] - dp - Dst : 0.f;
+        rsub = Rgw;
+        have_cand = false;  // an h beyond rl refilters the stage, then rebuilds the lists
+        fresh = false;
+        need_list = false;
+        // the stored lists serve only if every starting h lies within them
+        need_filter = __any_sync(0xffffffffu, has && it.h > rl);
+      }
+    }
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int pass = 0; pass < a.max_iter; ++pass) {
       if (mode < 2 && __any_sync(0xffffffffu, need_filter)) {
-        // sub-cluster radius: its largest h x the list skin, capped by Rg
+        // sub-cluster radius: its largest h x the list skin, capped by Rgw
         float hm = has && !fin ? it.h : 0.f;
         for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-        rsub = fminf(hm * a.skin_list, Rg);
+        rsub = fminf(hm * a.skin_list, Rgw);
         ncand = filter_stage<false>(S.stage, nullptr, sr, blo, bhi, rsub, cand, kCandD, lane);
         need_filter = false;
+        have_cand = true;
         need_list = !fin;
         if (ncand > kCandD) mode = 2;  // ncand is warp-uniform
       }
@@ -842,10 +1087,11 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
           }
         }
         need_list = false;
+        fresh = true;
         if (__any_sync(0xffffffffu, cnt > LANE)) {
           mode = 1;
         } else {  // pad every lane's list with the sentinel to the warp's longest, x4
-          const int tpad = (warp_max_int(cnt) + 3) & ~3;
+          tpad = (warp_max_int(cnt) + 3) & ~3;
           for (int t = cnt; t < tpad; ++t) list[t * 32 + lane] = (unsigned short)NS;
         }
         __syncwarp();
@@ -885,13 +1131,14 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
           fin = true;
           fs = tot;
           ngb = ctot - 1;  // the self term is always inside
-        } else if (it.h > rsub) {
+        } else if (it.h > rsub || (it.h > rl && !have_cand)) {
           need_filter = true;
         } else if (it.h > rl) {
           need_list = true;
         }
       }
-      const float Rown = TIGHT && has ? S.tgt[tloc].w : Rg;  // this target's staged radius
+      // this target's staged radius
+      const float Rown = TIGHT && has ? S.tgt[tloc].w : (tightw ? Rtight : Rgw);
       if (__any_sync(0xffffffffu, !fin && it.h > Rown)) {
         failed = true;  // beyond the staged radius
         break;
@@ -901,8 +1148,25 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     if (lane == 0 && mode) ++n_direct[mode - 1];
     if (failed || !__all_sync(0xffffffffu, fin)) {
       // this warp's unfinished targets go to the third tier (done is not set)
-      if (lane == 0) a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + warp;
+      if (lane == 0) {
+        a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + warp;
+        if (use_cache) M->wok[warp] = 0;
+      }
       continue;
+    }
+    if (use_cache) {  // keep this warp's lists for the force and later calls
+      if (mode == 0 && fresh) {
+        const size_t lrow = ((size_t)g * kNW + warp) * a.cache.lane_cap * 32;
+        for (int t = 0; t < tpad; ++t) a.cache.list[lrow + t * 32 + lane] = list[t * 32 + lane];
+        if (has && slice == 0) a.cache.rl[i] = rl;
+      }
+      if (lane == 0) {
+        if (mode != 0)
+          M->tpad[warp] = -1;
+        else if (fresh)
+          M->tpad[warp] = tpad;
+        M->wok[warp] = mode == 0 && !tightw;  // the force needs the stage complete within Rg
+      }
     }
     if (has && slice == 0) {
       float rho, omega, P;
@@ -935,6 +1199,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     if (n_direct[0]) atomicAdd(&a.ctr->direct[0], n_direct[0]);
     if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
+  if (n_built) atomicAdd(&a.ctr->cache_built, n_built);
 }
 
 // One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
@@ -1288,18 +1553,50 @@ __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a)
   }
 }
 
-template <bool KAHAN, int NS>
+template <bool KAHAN, int NS, bool REUSE = false>
 void launch_density_tier(const BatchDensArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
   const int bytes = (int)sizeof(DensSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_density_batched<KAHAN, NS>,
+    cudaFuncSetAttribute(k_density_batched<KAHAN, NS, REUSE>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
-  k_density_batched<KAHAN, NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
+  k_density_batched<KAHAN, NS, REUSE><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
 }
+
+// The first tier: with the neighbour cache, the groups on their stored stage
+// first, then those that stage anew.
+template <bool KAHAN, int NS>
+void launch_density_first(const BatchDensArgs &a, int blocks, cudaStream_t s) {
+  if (a.cache_on) launch_density_tier<KAHAN, NS, true>(a, 0, blocks, s);
+  launch_density_tier<KAHAN, NS, false>(a, 0, blocks, s);
+}
+
+__global__ void k_cache_init(CacheCtl *ctl, int n_groups) {
+  ctl->build_all = 1;
+  ctl->fail = 0;
+  ctl->n_groups = n_groups;
+}
+
+void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s) {
+  k_cache_init<<<1, 1, 0, s>>>(ctl, n_groups);
+  note_launch();
+}
+
+__global__ void k_cache_decide(CacheCtl *ctl) {
+  ctl->build_all = ctl->fail * 8 > ctl->n_groups ? 1 : 0;
+  ctl->fail = 0;
+}
+
+void launch_cache_decide(CacheCtl *ctl, cudaStream_t s) {
+  k_cache_decide<<<1, 1, 0, s>>>(ctl);
+  note_launch();
+}
+
+int cache_stage_slots(int tile) { return tile ? kStageDL : kStageD; }
+int cache_lane_cap(int tile) { return dens_lane(tile ? kStageDL : kStageD); }
 
 // Tier 0 over every group, then tier 1 (4x the stage, 2 blocks per SM) over
 // the groups tier 0 queued; `a.ctr->queued` and `a.queue` must be zeroed /
@@ -1310,16 +1607,16 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
   if (a.kahan) {
     if (a.tile)
-      launch_density_tier<true, kStageDL>(a, 0, blocks, s);
+      launch_density_first<true, kStageDL>(a, blocks, s);
     else
-      launch_density_tier<true, kStageD>(a, 0, blocks, s);
+      launch_density_first<true, kStageD>(a, blocks, s);
     launch_density_tier<true, kBigStageD>(a, 1, big, s);
     k_density_stream<true><<<152 * 8, 128, 0, s>>>(a);
   } else {
     if (a.tile)
-      launch_density_tier<false, kStageDL>(a, 0, blocks, s);
+      launch_density_first<false, kStageDL>(a, blocks, s);
     else
-      launch_density_tier<false, kStageD>(a, 0, blocks, s);
+      launch_density_first<false, kStageD>(a, blocks, s);
     launch_density_tier<false, kBigStageD>(a, 1, big, s);
     k_density_stream<false><<<152 * 8, 128, 0, s>>>(a);
   }
@@ -1350,6 +1647,7 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
   for (int q = blockIdx.x; q < ng; q += gridDim.x) {
     const int g = tier_group(tier, q, a.queue);
+    if (tier == 0 && a.cache_on && a.cache.fuse[g]) continue;  // done on the cache
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
@@ -1547,6 +1845,147 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
 
 }
 
+// ------------------------------------------------- force on the cache
+//
+// Groups whose density finished in the first tier on per-lane lists, with no
+// particle outside their stage able to reach them (fuse[g], set by the
+// far-reacher walk), take the force from the density's stored stage and
+// lists: no walk, no staging tests, no filter, no list build. A target's
+// pairs r < max(h_i, h_j) are (a) its listed entries, each tested, and (b)
+// staged j whose own h reaches it from beyond its list: a staged j missing
+// from i's list lies at r >= rl_i - dpath_i - D >= thr (the list's radius
+// less the motion since it was built), so only j with h_j > thr can add a
+// pair; those are taken from the stage 32 at a time, and a per-target bitmap
+// of the listed entries keeps each pair once.
+template <int NSD>
+struct ForceReuseSmem {
+  unsigned dmax_bits;
+  unsigned pad_[3];
+  float4 sq[NSD + 1];                  // position in the group frame, m; [NSD] sentinel
+  float2 sf[NSD + 1];                  // A (8/pi) h^-4, h^2
+  int sj[NSD + 1];                     // particle index
+  unsigned bm[kNW][kSub][(NSD + 32) / 32];  // listed stage entries per target
+};
+
+constexpr int force_reuse_min_blocks(int nsd) { return nsd == kStageD ? 6 : 4; }
+
+template <bool KAHAN, int NSD>
+__global__ void __launch_bounds__(kNW * 32, force_reuse_min_blocks(NSD))
+    k_force_reuse(BatchForceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ForceReuseSmem<NSD> &S = *reinterpret_cast<ForceReuseSmem<NSD> *>(smem_raw);
+  constexpr int BMW = (NSD + 32) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slice = lane & (kSlice - 1);
+  unsigned long long ntest = 0, inter = 0;
+  if (threadIdx.x == 0) {  // read after a barrier
+    S.sq[NSD] = make_float4(kFar, kFar, kFar, 0.f);
+    S.sf[NSD] = make_float2(0.f, 1.f);
+    S.sj[NSD] = 0;
+  }
+  const CacheArgs &C = a.cache;
+  for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x) {
+    if (!C.fuse[g]) continue;  // block-uniform
+    const Group G = a.groups[g];
+    const GroupCache &M = C.meta[g];
+    int wc[4];
+    for (int w = 0; w < 4; ++w) wc[w] = M.wc[w];
+    float Dst;
+    const StageRange sr = load_stage_cached<true>(C, g, wc, C.tasks + (size_t)g * a.tcap, a.pm,
+                                                  a.fi, S.sq, S.sf, S.sj, NSD, &S.dmax_bits, &Dst);
+    const int tloc = warp * kSub + (lane >> 2);
+    const bool has = tloc < G.count;
+    if (!__any_sync(0xffffffffu, has)) continue;
+    const int i = G.start + tloc;
+    float px = 0.f, py = 0.f, pz = 0.f, thr = 3e38f;
+    float4 fi = make_float4(1.f, 1.f, 0.f, -1.f), vi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (has) {
+      const float4 q = a.gpos[i];
+      px = q.x;
+      py = q.y;
+      pz = q.z;
+      fi = a.fi[i];
+      vi = a.vu[i];
+      thr = C.rl[i] - C.dpath[i] - Dst;
+    }
+    for (int o = 16; o; o >>= 1) thr = fminf(thr, __shfl_xor_sync(0xffffffffu, thr, o));
+    const float thr2 = thr > 0.f ? thr * thr : -1.f;
+    unsigned *bm = S.bm[warp][lane >> 2];
+    for (int t = lane; t < kSub * BMW; t += 32) S.bm[warp][t / BMW][t % BMW] = 0u;
+    __syncwarp();
+    const int tp = M.tpad[warp];
+    const size_t lrow = ((size_t)g * kNW + warp) * C.lane_cap * 32;
+    ForceAcc<KAHAN> acc;
+    // (a) listed entries (sentinel padded, x4)
+    for (int t = 0; t < tp; t += 4) {
+      int k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = C.list[lrow + (t + u) * 32 + lane];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!has) continue;
+        if (k[u] < NSD) atomicOr(&bm[k[u] >> 5], 1u << (k[u] & 31));
+        acc.add(S, k[u], a.vu, px, py, pz, fi, vi, fi.w, NSD);
+      }
+    }
+    if (has) ntest += tp;
+    __syncwarp();
+    // (b) staged j with h_j > thr, not listed for the target, r < h_j
+    int turn = 0;
+    for (int tb = 0; tb < sr.total; tb += 32) {
+      const int t = tb + lane;
+      int k = NSD;
+      bool in = false;
+      if (t < sr.total) {
+        k = sr.index(t);
+        in = S.sf[k].y > thr2;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, in);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int kk = __shfl_sync(0xffffffffu, k, src);
+        const bool listed = (bm[kk >> 5] >> (kk & 31)) & 1u;
+        if (has && !listed && slice == (turn & 3)) {
+          acc.add(S, kk, a.vu, px, py, pz, fi, vi, fi.w, NSD);
+          ++ntest;
+        }
+        ++turn;
+      }
+    }
+    const float ax = slice_sum(acc.ax), ay = slice_sum(acc.ay), az = slice_sum(acc.az),
+                du = slice_sum(acc.du);
+    int ctot = acc.c;
+    ctot += __shfl_xor_sync(0xffffffffu, ctot, 1);
+    ctot += __shfl_xor_sync(0xffffffffu, ctot, 2);
+    if (has && slice == 0) {
+      a.acc[i] = make_float4(ax, ay, az, du);
+      a.nforce[i] = ctot;
+      a.fdone[i] = 1;
+      inter += (unsigned long long)ctot;
+    }
+  }
+  ntest = warp_sum(ntest);
+  inter = warp_sum(inter);
+  if (lane == 0) {
+    if (ntest) atomicAdd(&a.ctr->force_cand, ntest);
+    if (inter) atomicAdd(&a.ctr->force_inter, inter);
+  }
+}
+
+template <bool KAHAN, int NSD>
+void launch_force_reuse(const BatchForceArgs &a, int blocks, cudaStream_t s) {
+  static bool attr = false;
+  const int bytes = (int)sizeof(ForceReuseSmem<NSD>);
+  if (!attr) {
+    cudaFuncSetAttribute(k_force_reuse<KAHAN, NSD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         bytes);
+    attr = true;
+  }
+  k_force_reuse<KAHAN, NSD><<<blocks, kNW * 32, bytes, s>>>(a);
+  note_launch();
+}
+
 template <bool KAHAN, int NS>
 void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
@@ -1564,6 +2003,19 @@ void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
   const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
+  if (a.cache_on) {  // groups on the density's cache first (fuse[g]); the tiers skip them
+    if (a.kahan) {
+      if (a.tile)
+        launch_force_reuse<true, kStageDL>(a, blocks, s);
+      else
+        launch_force_reuse<true, kStageD>(a, blocks, s);
+    } else {
+      if (a.tile)
+        launch_force_reuse<false, kStageDL>(a, blocks, s);
+      else
+        launch_force_reuse<false, kStageD>(a, blocks, s);
+    }
+  }
   if (a.kahan) {
     if (a.tile)
       launch_force_tier<true, kStageFL>(a, 0, blocks, s);

@@ -130,8 +130,36 @@ void launch_permute(const StoreArrays &dst, const StoreArrays &src, const int *o
 template <bool SAVE>
 __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int nb,
                              float gm1, float *hf, StoreArrays save, unsigned char *done,
-                             unsigned char *fdone, DevCounters *ctr) {
+                             unsigned char *fdone, DevCounters *ctr, DriftCache dc) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  // neighbour-cache bookkeeping: path length since the epoch began (an upper
+  // bound of the displacement) and its largest value per top cell, one
+  // atomic per warp where the warp's particles share a cell (the usual case
+  // in the cell-sorted store)
+  float dp = 0.f;
+  int cell = -1;
+  if (s < n && dc.dpath) {
+    const float4 a = st.acc[s];
+    const float4 v = st.vu[s];
+    const float hdt = (float)(0.5 * dt);
+    const float vx = fmaf(a.x, hdt, v.x), vy = fmaf(a.y, hdt, v.y), vz = fmaf(a.z, hdt, v.z);
+    const float step = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))) * (float)dt;
+    // rounding of |v dt| and of the sum: a relative 1e-6 keeps it an upper bound
+    dp = dc.ctl->build_all ? 0.f : (dc.dpath[s] + step * (1.f + 1e-6f)) * (1.f + 1e-6f);
+    dc.dpath[s] = dp;
+    cell = dc.nodes[dc.leaves[dc.leaf_of[s]].node].cell;
+  }
+  if (dc.dpath) {  // dp >= 0: its bit pattern orders like an unsigned integer
+    const int c0 = __shfl_sync(0xffffffffu, cell, 0);
+    if (__all_sync(0xffffffffu, cell == c0 || cell < 0)) {
+      float m = dp;
+      for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0 && c0 >= 0 && m > 0.f) atomicMax(&dc.dmax_cell[c0], __float_as_uint(m));
+    } else if (cell >= 0 && dp > 0.f) {
+      atomicMax(&dc.dmax_cell[cell], __float_as_uint(dp));
+    }
+  }
   if (s >= n) return;
   if (done) done[s] = 0;
   if (fdone) fdone[s] = 0;
@@ -169,14 +197,16 @@ __global__ void k_kick_drift(StoreArrays st, int n, double dt, const BoxDev *box
 
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
                        double gamma, float *hf, const StoreArrays *save, unsigned char *done,
-                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s) {
+                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s,
+                       const DriftCache *dcp) {
   const float gm1 = (float)(gamma - 1.0);
+  const DriftCache dc = dcp ? *dcp : DriftCache{};
   if (save)
     k_kick_drift<true><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf, *save,
-                                                       done, fdone, ctr);
+                                                       done, fdone, ctr, dc);
   else
     k_kick_drift<false><<<(n + 255) / 256, 256, 0, s>>>(st, n, dt, boxes, n_boxes, gm1, hf,
-                                                        StoreArrays{}, done, fdone, ctr);
+                                                        StoreArrays{}, done, fdone, ctr, dc);
   note_launch();
 }
 

@@ -77,7 +77,7 @@ struct sph_ctx {
 
   // growable, library-owned
   // batched form: target groups and their task lists
-  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue, lflag;
+  DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue, lflag, gwmode;
   int n_groups = 0;
   bool groups_valid = false;
   int64_t n_gd_tasks = 0, n_gf_tasks = 0;
@@ -85,6 +85,12 @@ struct sph_ctx {
       dens_off, dens_tasks, force_off, force_tasks;
   int n_cells = 0, n_nodes = 0, n_leaves = 0;
   int64_t n_dens_tasks = 0, n_force_tasks = 0;
+
+  // neighbour cache of the batched form: the density's stage and per-lane
+  // lists kept in HBM for the force and for later calls
+  DevBuf vc_meta, vc_sj, vc_slot, vc_list, vc_rl, vc_dpath, vc_dmax, vc_gmode, vc_fuse, vc_ctl;
+  bool vc_valid = false;  // laid out for the current groups and tile, epoch started
+  int vc_tile = -1;
 
   DevCounters *ctr = nullptr;    // device
   DevCounters *ctr_h = nullptr;  // pinned host mirror
@@ -694,6 +700,67 @@ int build_groups(sph_ctx *c) {
   launch_group_geometry(ga, c->stream);
   c->groups_valid = true;
   c->groups_geom_valid = true;
+  c->vc_valid = false;  // new groups and particle order: the cache starts a new epoch
+  return sync_check(c);
+}
+
+bool cache_on(const sph_ctx *c) { return c->p.mode == SPH_MODE_BATCHED && c->p.reuse_lists; }
+
+CacheArgs cache_args(sph_ctx *c) {
+  CacheArgs a{};
+  a.meta = as<GroupCache>(c->vc_meta);
+  a.sj = as<int>(c->vc_sj);
+  a.slot = as<unsigned short>(c->vc_slot);
+  a.list = as<unsigned short>(c->vc_list);
+  a.rl = as<float>(c->vc_rl);
+  a.dpath = as<float>(c->vc_dpath);
+  a.dmax_cell = as<unsigned>(c->vc_dmax);
+  a.gmode = as<unsigned char>(c->vc_gmode);
+  a.fuse = as<unsigned char>(c->vc_fuse);
+  a.ctl = as<CacheCtl>(c->vc_ctl);
+  a.tasks = as<Task>(c->gd_tasks);
+  a.ns = cache_stage_slots(c->p.tile);
+  a.lane_cap = cache_lane_cap(c->p.tile);
+  return a;
+}
+
+DriftCache drift_cache(sph_ctx *c) {
+  DriftCache d{};
+  d.dpath = as<float>(c->vc_dpath);
+  d.dmax_cell = as<unsigned>(c->vc_dmax);
+  d.ctl = as<CacheCtl>(c->vc_ctl);
+  d.leaf_of = c->leaf_of;
+  d.leaves = as<Leaf>(c->leaves);
+  d.nodes = as<Node>(c->nodes);
+  return d;
+}
+
+// Lay the neighbour cache out for the current groups and tile and start a new
+// epoch (every group builds; path lengths from zero). Not inside a capture:
+// the steady step is captured only once a density has prepared it.
+int cache_prepare(sph_ctx *c) {
+  if (!cache_on(c) || (c->vc_valid && c->vc_tile == c->p.tile)) return SPH_OK;
+  if (c->capturing) return fail(c, SPH_ESTATE, "neighbour cache laid out inside a capture");
+  const size_t ng = (size_t)std::max(c->n_groups, 1), n = (size_t)std::max(c->n, 1);
+  const size_t ns = (size_t)cache_stage_slots(c->p.tile), lc = (size_t)cache_lane_cap(c->p.tile);
+  TRY(ensure(c, c->vc_meta, sizeof(GroupCache) * ng));
+  TRY(ensure(c, c->vc_sj, sizeof(int) * ng * ns));
+  TRY(ensure(c, c->vc_slot, sizeof(unsigned short) * ng * ns));
+  TRY(ensure(c, c->vc_list, sizeof(unsigned short) * ng * 4 * lc * 32));
+  TRY(ensure(c, c->vc_rl, sizeof(float) * n));
+  TRY(ensure(c, c->vc_dpath, sizeof(float) * n));
+  TRY(ensure(c, c->vc_dmax, sizeof(unsigned) * (size_t)std::max(c->n_cells, 1)));
+  TRY(ensure(c, c->vc_gmode, ng));
+  TRY(ensure(c, c->vc_fuse, ng));
+  TRY(ensure(c, c->vc_ctl, sizeof(CacheCtl)));
+  CUDA_TRY(cudaMemsetAsync(c->vc_meta.p, 0, sizeof(GroupCache) * ng, c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->vc_dpath.p, 0, sizeof(float) * n, c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->vc_dmax.p, 0, sizeof(unsigned) * (size_t)std::max(c->n_cells, 1),
+                           c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->vc_fuse.p, 0, ng, c->stream));
+  launch_cache_init(as<CacheCtl>(c->vc_ctl), c->n_groups, c->stream);
+  c->vc_valid = true;
+  c->vc_tile = c->p.tile;
   return sync_check(c);
 }
 
@@ -710,6 +777,7 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &t
   const int ng = c->n_groups;
   TRY(ensure(c, cnt, sizeof(int) * (size_t)std::max(ng, 1)));
   TRY(ensure(c, tasks, sizeof(Task) * (size_t)std::max(ng, 1) * kTaskCap));
+  TRY(ensure(c, c->gwmode, (size_t)std::max(ng, 1)));
   GroupListArgs la{};
   la.n_groups = ng;
   la.groups = as<Group>(c->groups);
@@ -727,6 +795,10 @@ int build_group_lists(sph_ctx *c, bool force, float skin, DevBuf &cnt, DevBuf &t
   la.hf = c->hf;
   la.walk_queue = as<int>(c->gqueue);  // free until the interaction kernels run
   la.walk_queued = &c->ctr->walk_queued;
+  la.ctr = c->ctr;
+  la.wmode = force ? nullptr : as<unsigned char>(c->gwmode);
+  la.cache_on = cache_on(c) && c->vc_valid;
+  if (la.cache_on) la.cache = cache_args(c);
   CUDA_TRY(cudaMemsetAsync(la.walk_queued, 0, sizeof(int), c->stream));
   launch_group_lists(la, c->stream);
   toc(c, stage);
@@ -750,8 +822,18 @@ constexpr float kSkinList = 1.02f;
 // walk, the three tiers), no host reads.
 // `hmax_current`: the node and group h maxima still hold for the current h
 // (a steady step: h has not changed since the last force's walk).
-int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P, bool hmax_current = false) {
+// Which (v, u) the pressure and the force use: the current ones, or those
+// predicted to the end of a step. Passed as a choice, not a pointer: a regrid
+// inside a call permutes the store by swapping its two copies, so the array
+// is looked up at each use.
+enum VuSel { kVuCurrent = 0, kVuPredicted = 1 };
+const float4 *vu_of(const sph_ctx *c, VuSel sel) {
+  return sel == kVuPredicted ? c->st.vu_pred : c->st.vu;
+}
+
+int enqueue_density_batched(sph_ctx *c, VuSel vu_for_P, bool hmax_current = false) {
   if (!c->groups_valid) TRY(build_groups(c));
+  TRY(cache_prepare(c));
   if (!c->groups_geom_valid) {  // positions moved on an unchanged grid
     launch_group_geometry(group_args(c), c->stream);
     c->groups_geom_valid = true;
@@ -773,7 +855,7 @@ int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P, bool hmax_curren
   da.boxes = c->boxes_d;
   da.h = c->st.h;
   da.hf = c->hf;
-  da.vu = vu_for_P;
+  da.vu = vu_of(c, vu_for_P);
   da.n_ngb = c->p.n_ngb;
   da.tol = c->p.h_tol;
   da.gamma = c->p.gamma;
@@ -794,14 +876,18 @@ int enqueue_density_batched(sph_ctx *c, const float4 *vu_for_P, bool hmax_curren
   da.gpos = c->gpos;
   da.tile = c->p.tile;
   da.nodes = as<Node>(c->nodes);
+  da.wmode = as<unsigned char>(c->gwmode);
+  da.cache_on = cache_on(c) && c->vc_valid;
+  if (da.cache_on) da.cache = cache_args(c);
   tic(c, kDens);
   launch_density_batched(da, c->stream);
   toc(c, kDens);
+  if (da.cache_on) launch_cache_decide(da.cache.ctl, c->stream);
   ++c->dens_launches;
   return sync_check(c);
 }
 
-int density_batched(sph_ctx *c, const float4 *vu_for_P) {
+int density_batched(sph_ctx *c, VuSel vu_for_P) {
   TRY(enqueue_density_batched(c, vu_for_P));
   TRY(read_counters(c));
   TRY(check_status(c, c->ctr_h->status));
@@ -809,7 +895,7 @@ int density_batched(sph_ctx *c, const float4 *vu_for_P) {
   return SPH_OK;
 }
 
-int density_impl(sph_ctx *c, const float4 *vu_for_P) {
+int density_impl(sph_ctx *c, VuSel vu_for_P) {
   if (!c->grid_valid) TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
   const int n = c->n;
   launch_h_guess(geom_args(c), c->p.n_ngb, c->st.h, c->hf, c->stream);
@@ -892,7 +978,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
     gh.hf = c->hf;
     gh.sums = c->sums;
     gh.cnt = c->cnt;
-    gh.vu = vu_for_P;
+    gh.vu = vu_of(c, vu_for_P);
     gh.done = c->done;
     gh.niter = c->niter;
     gh.nngb = c->nngb;
@@ -935,7 +1021,7 @@ int density_impl(sph_ctx *c, const float4 *vu_for_P) {
 // `steady`: called from a steady step, whose start zeroed every counter and
 // whose kick-drift cleared the force finished flags (the density writes none
 // of the force's counters; any fallback there redoes the step).
-int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool steady = false) {
+int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
   if (!c->groups_valid) TRY(build_groups(c));
   GroupBuildArgs gb = group_args(c);
   launch_group_hmax(gb, c->stream);
@@ -960,7 +1046,7 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool steady = 
   fa.leaf_of = c->leaf_of;
   fa.pm = c->pm;
   fa.fi = c->fi;
-  fa.vu = vu_for_force;
+  fa.vu = vu_of(c, vu_for_force);
   fa.acc = c->st.acc;
   fa.nforce = c->nforce;
   fa.fdone = c->fdone;
@@ -972,6 +1058,8 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool steady = 
   fa.nodes = as<Node>(c->nodes);
   fa.boxes = c->boxes_d;
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
+  fa.cache_on = cache_on(c) && c->vc_valid;
+  if (fa.cache_on) fa.cache = cache_args(c);
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -981,7 +1069,7 @@ int enqueue_force_batched(sph_ctx *c, const float4 *vu_for_force, bool steady = 
 
 // Batched force; returns through *all_done whether every particle was
 // finished (else the per-leaf form must run).
-int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
+int force_batched(sph_ctx *c, VuSel vu_for_force, bool *all_done) {
   *all_done = false;
   TRY(enqueue_force_batched(c, vu_for_force));
   TRY(read_counters(c));
@@ -991,7 +1079,7 @@ int force_batched(sph_ctx *c, const float4 *vu_for_force, bool *all_done) {
   return SPH_OK;
 }
 
-int force_impl(sph_ctx *c, const float4 *vu_for_force) {
+int force_impl(sph_ctx *c, VuSel vu_for_force) {
   if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
   if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
   const int *active = nullptr;
@@ -1031,7 +1119,7 @@ int force_impl(sph_ctx *c, const float4 *vu_for_force) {
   fa.tasks = as<Task>(c->force_tasks);
   fa.pm = c->pm;
   fa.fi = c->fi;
-  fa.vu = vu_for_force;
+  fa.vu = vu_of(c, vu_for_force);
   fa.acc = c->st.acc;
   fa.nforce = c->nforce;
   fa.ctr = c->ctr;
@@ -1087,9 +1175,13 @@ void copy_step_state(sph_ctx *c, const StoreArrays &from, const StoreArrays &to)
 int step_once(sph_ctx *c, double dt, bool reuse) {
   c->regrids_in_step = 0;
   CUDA_TRY(cudaMemsetAsync(&c->ctr->step_status, 0, sizeof(int), c->stream));
+  const bool vc = cache_on(c) && c->vc_valid;
+  if (vc) CUDA_TRY(cudaMemsetAsync(c->vc_dmax.p, 0, sizeof(unsigned) * c->n_cells, c->stream));
+  const DriftCache dc = drift_cache(c);
   tic(c, kInteg);
   launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf,
-                    reuse ? &c->st2 : nullptr, nullptr, nullptr, c->ctr, c->stream);
+                    reuse ? &c->st2 : nullptr, nullptr, nullptr, c->ctr, c->stream,
+                    vc ? &dc : nullptr);
   toc(c, kInteg);
   c->density_valid = false;
   c->force_valid = false;
@@ -1099,8 +1191,8 @@ int step_once(sph_ctx *c, double dt, bool reuse) {
     c->grid_valid = false;
     TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
   }
-  TRY(density_impl(c, c->st.vu_pred));
-  TRY(force_impl(c, c->st.vu_pred));
+  TRY(density_impl(c, kVuPredicted));
+  TRY(force_impl(c, kVuPredicted));
   tic(c, kInteg2);
   launch_kick(c->st, c->n, dt, c->ctr, c->stream);
   toc(c, kInteg2);
@@ -1117,8 +1209,11 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   // also clears the density and force finished flags (the batched tiers keep
   // their h brackets in registers, so nothing else of the iteration state
   // needs resetting)
+  const bool vc = cache_on(c) && c->vc_valid;
+  if (vc) CUDA_TRY(cudaMemsetAsync(c->vc_dmax.p, 0, sizeof(unsigned) * c->n_cells, c->stream));
+  const DriftCache dc = drift_cache(c);
   launch_kick_drift(c->st, c->n, dt, c->boxes_d, c->nb, c->p.gamma, c->hf, &c->st2, c->done,
-                    c->fdone, c->ctr, c->stream);
+                    c->fdone, c->ctr, c->stream, vc ? &dc : nullptr);
   toc(c, kInteg);
   tic(c, kGrid);
   CUDA_TRY(cudaMemsetAsync(c->boxout, 0, sizeof(unsigned) * (size_t)c->nb, c->stream));
@@ -1133,8 +1228,8 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
   // finished by the third tier
   launch_group_geometry(group_args(c), c->stream);
   c->groups_geom_valid = true;
-  TRY(enqueue_density_batched(c, c->st.vu_pred, true));
-  TRY(enqueue_force_batched(c, c->st.vu_pred, true));
+  TRY(enqueue_density_batched(c, kVuPredicted, true));
+  TRY(enqueue_force_batched(c, kVuPredicted, true));
   tic(c, kInteg2);
   launch_kick(c->st, c->n, dt, c->ctr, c->stream);
   toc(c, kInteg2);
@@ -1147,6 +1242,7 @@ int enqueue_steady_step(sph_ctx *c, double dt) {
 // default stream, which cannot be captured); host-side counters that the
 // capture advanced are taken back and replayed per launch.
 int capture_steady_step(sph_ctx *c, double dt) {
+  TRY(cache_prepare(c));
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -1227,6 +1323,7 @@ void sph_default_params(sph_params *p) {
   p->reuse_grid = 1;
   p->tile = 0;
   p->cell_factor = 2.0;
+  p->reuse_lists = 1;
 }
 
 int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
@@ -1240,7 +1337,8 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
       (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
-      (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0))
+      (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
+      (q.reuse_lists != 0 && q.reuse_lists != 1))
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;
@@ -1332,7 +1430,7 @@ int sph_density(sph_ctx *c) {
   LaunchScope ls(c);
   c->err.clear();
   if (!c->loaded) return fail(c, SPH_ESTATE, "sph_density before sph_init");
-  return density_impl(c, c->st.vu);
+  return density_impl(c, kVuCurrent);
 }
 
 int sph_force(sph_ctx *c) {
@@ -1340,7 +1438,7 @@ int sph_force(sph_ctx *c) {
   LaunchScope ls(c);
   c->err.clear();
   if (!c->loaded) return fail(c, SPH_ESTATE, "sph_force before sph_init");
-  return force_impl(c, c->st.vu);
+  return force_impl(c, kVuCurrent);
 }
 
 int sph_step(sph_ctx *c, double dt, int n_steps) {
@@ -1439,7 +1537,7 @@ int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_facto
   const double factors[] = {1.5, 2.0, 2.5, 3.0};
   double best = 1e300;
   sph_params best_p = keep;
-  int rc = density_impl(c, c->st.vu);  // converged h to start from
+  int rc = density_impl(c, kVuCurrent);  // converged h to start from
   for (int t = 0; t < tiles && rc == SPH_OK; ++t)
     for (int ns : splits)
       for (double cf : factors) {
@@ -1452,8 +1550,8 @@ int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_facto
         double ms_min = 1e300;
         for (int rep = 0; rep < 2 && rc == SPH_OK; ++rep) {
           cudaEventRecord(e0, c->stream);
-          rc = density_impl(c, c->st.vu);
-          if (rc == SPH_OK) rc = force_impl(c, c->st.vu);
+          rc = density_impl(c, kVuCurrent);
+          if (rc == SPH_OK) rc = force_impl(c, kVuCurrent);
           cudaEventRecord(e1, c->stream);
           if (rc == SPH_OK && cudaEventSynchronize(e1) == cudaSuccess) {
             float ms = 0.f;
@@ -1472,8 +1570,8 @@ int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_facto
   c->grid_reusable = false;
   if (rc != SPH_OK) return rc;
   TRY(build_grid(c, false, nullptr, nullptr, nullptr, nullptr));
-  TRY(density_impl(c, c->st.vu));
-  TRY(force_impl(c, c->st.vu));
+  TRY(density_impl(c, kVuCurrent));
+  TRY(force_impl(c, kVuCurrent));
   if (tile_out) *tile_out = c->p.tile;
   if (n_split_out) *n_split_out = c->p.n_split;
   if (cell_factor_out) *cell_factor_out = c->p.cell_factor;
@@ -1539,6 +1637,10 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->reused_steps = c->reused_steps;
   out->graph_steps = c->graph_steps;
   out->redone_steps = c->redone_steps;
+  out->n_groups = c->n_groups;
+  out->cache_density_groups = c->ctr_h->cache_used[0];
+  out->cache_force_groups = c->ctr_h->cache_used[1];
+  out->cache_built_groups = c->ctr_h->cache_built;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
   double hmin = 0, hmax = 0;
@@ -1557,7 +1659,9 @@ void sph_destroy(sph_ctx *c) {
                     &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
                     &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
-                    &c->gqueue,     &c->lflag};
+                    &c->gqueue,     &c->lflag,      &c->gwmode,   &c->vc_meta,    &c->vc_sj,
+                    &c->vc_slot,    &c->vc_list,    &c->vc_rl,    &c->vc_dpath,   &c->vc_dmax,
+                    &c->vc_gmode,   &c->vc_fuse,    &c->vc_ctl};
   for (DevBuf *b : bufs) release(*b);
   for (void *p : c->owned) cudaFree(p);
   if (c->ctr) cudaFree(c->ctr);

@@ -98,6 +98,9 @@ struct DevCounters {
   int why[4];                         // batched fallbacks: density third-tier walk (frontier
                                       // or h beyond the top cell), density passes, force
                                       // third-tier walk, (zero)
+  int cache_used[2];                  // groups whose density / force ran on the stored
+                                      // neighbour cache (no walk, no staging tests)
+  int cache_built;                    // groups whose density built (and stored) a new cache
   int step_status;                    // kErr* bits of the kicks and the grid check (last
                                       // field: the density's counter reset keeps it)
 };
@@ -139,10 +142,17 @@ struct HIter {
   }
 };
 
+// Largest relative distance of an accepted h from the root, to first order:
+// |N - n_ngb| / (N s) with s = d ln N / d ln h. It keeps h well inside the
+// 1e-6 h band within which integer neighbour counts may differ from exact
+// arithmetic, also for particles whose N is flat in h (small s).
+constexpr float kHAcc = 5e-7f;
+
 // Weighted neighbour number N = (32/3) sum w and dN/dh = -(32/(3h)) sum q w'
 // from the FP32 sums at h. Returns true when h is accepted: |N - n_ngb| <=
-// tol_n (= h_tol n_ngb; this test is FP64), or the next step would move h by
-// at most 5e-7 h (the resolution of FP32 sums). Otherwise moves h by Newton
+// tol_n (= h_tol n_ngb; this test is FP64) and |N - n_ngb| <= kHAcc N s, or
+// the next step would move h by at most 5e-7 h (the resolution of FP32
+// sums). Otherwise moves h by Newton
 // on ln N(ln h) (exponent s = h N'/N = -(sum q w') / (sum w) measured, so
 // steep N near clusters does not overshoot), clamped to [h/8, 2h] and to
 // hcap (L/3), bisecting the bracket when the step leaves it or |f| failed to
@@ -154,9 +164,11 @@ struct HIter {
 __device__ __forceinline__ bool h_newton_step(HIter &it, float sw, float sqdw, double n_ngb,
                                               double tol_n, double hcap, int *st) {
   const double f = fma(32.0 / 3.0, (double)sw, -n_ngb);
-  if (fabs(f) <= tol_n) return true;
-  const double h = it.h;
   const float ff = (float)f;
+  if (fabs(f) <= tol_n && sw > 0.f &&
+      fabsf(ff) <= kHAcc * (32.f / 3.f) * sw * (-sqdw / sw))  // N s = (32/3) sum(-q w')
+    return true;
+  const double h = it.h;
   double lo = it.lo, hi = it.hi;
   if (f < 0.0)
     lo = h;
@@ -205,8 +217,8 @@ struct HIterF {
 __device__ __forceinline__ bool h_newton_step_f(HIterF &it, float sw, float sqdw, double n_ngb,
                                                 double tol_n, float hcap, int *st) {
   const double f = fma(32.0 / 3.0, (double)sw, -n_ngb);
-  if (fabs(f) <= tol_n) return true;
-  const float ff = (float)f;  // |f| > tol_n: no underflow, the sign survives
+  const float ff = (float)f;
+  if (fabs(f) <= tol_n && fabsf(ff) <= kHAcc * (32.f / 3.f) * -sqdw) return true;  // N s
   const float h = it.h;
   float lo = it.lo, hi = it.hi;
   if (ff < 0.f)
@@ -553,6 +565,60 @@ void launch_group_fill(const GroupBuildArgs &a, cudaStream_t s);
 void launch_group_geometry(const GroupBuildArgs &a, cudaStream_t s);
 void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s);
 
+// ---- neighbour cache of the batched form (density stage and per-lane
+// lists kept in HBM) ----
+//
+// The first tier of the density stores, per group, the particles of its
+// stage (index and task slot, in the stage's segment layout) and each warp's
+// per-lane neighbour lists (16-bit stage indices, padded to a multiple of 4
+// with the stage sentinel). The force of the same call reuses them: its
+// pairs r < max(h_i, h_j) are the listed ones, plus stage particles whose own
+// h reaches a target from beyond its list (found by a warp filter and
+// checked against the lists), plus particles outside the stage whose h
+// reaches the group (a walk that only follows nodes of large h: such a group
+// takes the full force path). Later density calls reuse a group's cache
+// while it is provably complete: dpath[i] bounds how far particle i has moved
+// since the cache epoch began (sum of |v dt| over the drifts), delta = the
+// largest dpath of the particles held by the 27 top cells around the group's
+// cell (on a reused grid every pair in range lies within them), D = the
+// stage's largest dpath. A stage built with
+// radius Rg around the group box then still holds every j with r_ij < Rg -
+// dpath_i - delta, and a list built with radius rl every staged j with r_ij <
+// rl - dpath_i - D: the kernel checks h_i against both and rebuilds the lists
+// (or sends the warp to the third tier) when h_i outgrows them.
+struct GroupCache {
+  int wc[4];       // staged entries per segment
+  int tpad[4];     // stored list rows per warp (-1: none stored)
+  int wok[4];      // the warp finished in the first tier on per-lane lists (last call)
+  float Rg;        // stage radius at the build (distance from the group box)
+  int stage_ok;    // the stored stage is complete (built in the first tier, no overflow)
+  int pad[2];
+};
+static_assert(sizeof(GroupCache) == 64, "GroupCache layout");
+
+struct CacheCtl {
+  int build_all;   // 1: the next density builds every group's cache (new epoch)
+  int fail;        // groups whose stored stage no longer covered their h (this call)
+  int n_groups;
+  int pad;
+};
+
+struct CacheArgs {
+  GroupCache *meta;        // [n_groups]
+  int *sj;                 // [n_groups * ns] particle index per stage slot
+  unsigned short *slot;    // [n_groups * ns] task slot per stage slot
+  unsigned short *list;    // [n_groups * 4 * lane_cap * 32] rows of 32 lanes
+  float *rl;               // [n] radius the particle's stored list was built with
+  float *dpath;            // [n] path length since the epoch began (upper bound)
+  const unsigned *dmax_cell; // [n_cells] largest dpath per top cell (float bits)
+  unsigned char *gmode;    // [n_groups] 1: this density call reuses the stored cache
+  unsigned char *fuse;     // [n_groups] 1: this force call reuses it
+  CacheCtl *ctl;
+  const Task *tasks;       // the density's task slots (the stored stage's shifts)
+  int ns;                  // stage slots per group (layout stride)
+  int lane_cap;            // list entries per lane (layout stride)
+};
+
 struct GroupListArgs {
   int n_groups;
   const Group *groups;
@@ -570,6 +636,13 @@ struct GroupListArgs {
   const float *hf;
   int *walk_queue;       // [n_groups] groups whose walk overflowed (null: no tight walk)
   int *walk_queued;      // device count of walk_queue, zero on entry
+  unsigned char *wmode;  // (density, optional) per group: 0 the group-box walk found its
+                         // tasks, 1 the tight walk did (each target's own sphere only)
+  int cache_on;          // the neighbour cache is in use (density: skip the walk of groups
+                         // whose stored stage is valid; force: far-reacher walk first, and
+                         // no walk for groups whose force reuses the cache)
+  CacheArgs cache;
+  DevCounters *ctr;
 };
 // The walk packs (node, neighbour code) into one int: node indices below 2^26.
 constexpr int kWalkMaxNodes = 1 << 26;
@@ -603,8 +676,22 @@ struct BatchDensArgs {
   int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
   const Node *nodes;     // the third tier walks the octrees itself
   int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
+  // per group, 1: its tasks came from the tight walk, so its stage is complete
+  // only within each target's own starting radius min(skin_stage h_i, w), not
+  // within Rg of the group box
+  const unsigned char *wmode;
+  int cache_on;
+  CacheArgs cache;
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
+// The next call's epoch decision (one thread): a new epoch when more than an
+// eighth of the groups had to rebuild their cache in this call.
+void launch_cache_decide(CacheCtl *ctl, cudaStream_t s);
+// A new epoch: every group builds (and stores) its cache in the next density.
+void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s);
+// Stage capacity and list entries per lane of the first tier of `tile`.
+int cache_stage_slots(int tile);
+int cache_lane_cap(int tile);
 
 struct BatchForceArgs {
   int n_groups;
@@ -628,6 +715,8 @@ struct BatchForceArgs {
   const BoxDev *boxes;
   int kahan;             // compensated sums
   int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
+  int cache_on;
+  CacheArgs cache;
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 
@@ -650,9 +739,22 @@ void launch_wrap_cell_keys_from_caller(const double *x, const BoxDev *boxes, int
 // copied there as they are read (the state a redone step restarts from);
 // done / fdone: when not null, the per-particle finished flags of the density
 // and force are cleared on the way
+// The neighbour cache's motion bound, updated by the drift (optional):
+// dpath[s] += |v dt| (or = 0 when ctl->build_all: the coming density starts
+// a new epoch), and dmax_cell[c] = max(dmax_cell[c], dpath) over the
+// particles of top cell c (zeroed by the caller).
+struct DriftCache {
+  float *dpath;
+  unsigned *dmax_cell;
+  const CacheCtl *ctl;
+  const int *leaf_of;
+  const Leaf *leaves;
+  const Node *nodes;
+};
 void launch_kick_drift(StoreArrays st, int n, double dt, const BoxDev *boxes, int n_boxes,
                        double gamma, float *hf, const StoreArrays *save, unsigned char *done,
-                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s);
+                       unsigned char *fdone, DevCounters *ctr, cudaStream_t s,
+                       const DriftCache *dc = nullptr);
 void launch_kick(StoreArrays st, int n, double dt, DevCounters *ctr, cudaStream_t s);
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
 void launch_leaf_of(const Leaf *leaves, int n_leaves, int *leaf_of, cudaStream_t s);

@@ -47,7 +47,8 @@ class sph_params(ctypes.Structure):
                 ("n_split", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mode", ctypes.c_int), ("profile", ctypes.c_int),
                 ("pair_sort", ctypes.c_int), ("reuse_grid", ctypes.c_int),
-                ("tile", ctypes.c_int), ("cell_factor", ctypes.c_double)]
+                ("tile", ctypes.c_int), ("cell_factor", ctypes.c_double),
+                ("reuse_lists", ctypes.c_int)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -73,7 +74,9 @@ class sph_stats_t(ctypes.Structure):
                 ("fallback_causes", ctypes.c_int32 * 4),
                 ("tier2_groups", ctypes.c_int32 * 2), ("tier3_entries", ctypes.c_int32 * 2),
                 ("sort_launches", ctypes.c_int64), ("reused_steps", ctypes.c_int64),
-                ("redone_steps", ctypes.c_int64), ("graph_steps", ctypes.c_int64)]
+                ("redone_steps", ctypes.c_int64), ("graph_steps", ctypes.c_int64),
+                ("n_groups", ctypes.c_int64), ("cache_density_groups", ctypes.c_int64),
+                ("cache_force_groups", ctypes.c_int64), ("cache_built_groups", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):
@@ -300,7 +303,8 @@ class Context:
                  mode: int = SPH_MODE_BATCHED, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
                  h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False,
                  pair_sort: bool = True, reuse_grid: bool = True, tile: int = 0,
-                 cell_factor: float = 2.0, stream=None, device="cuda"):
+                 cell_factor: float = 2.0, reuse_lists: bool = True, stream=None,
+                 device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -310,6 +314,7 @@ class Context:
         p.pair_sort = int(bool(pair_sort))
         p.reuse_grid = int(bool(reuse_grid))
         p.tile, p.cell_factor = int(tile), float(cell_factor)
+        p.reuse_lists = int(bool(reuse_lists))
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream

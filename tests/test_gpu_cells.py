@@ -106,13 +106,18 @@ def test_cells_exact_after_drift_with_and_without_regrid():
     _check(c, c.get("x").cpu().numpy())
     c.close()
     # reused grid: the cells stay those of the positions at the last regrid
+    # (a step regrids unless the grid of the previous one is known to reach)
     c = sph.Context(reuse_grid=True, cell_factor=1.0).load(p)
     c.density()
     c.force()
     x_regrid = c.get("x").cpu().numpy()
-    c.step(2e-3, 2)
-    st = c.stats()
-    assert st["reused_steps"] >= 1
-    if st["redone_steps"] == 0:
-        _check(c, x_regrid)
+    reused = redone = 0
+    for _ in range(3):
+        c.step(2e-3, 1)
+        st = c.stats()
+        if st["reused_steps"] == reused or st["redone_steps"] > redone:  # a regrid
+            x_regrid = c.get("x").cpu().numpy()
+        reused, redone = st["reused_steps"], st["redone_steps"]
+    assert reused - redone >= 1
+    _check(c, x_regrid)
     c.close()

@@ -86,6 +86,21 @@ def test_lognormal_small(mode):
     compare_force(g, s)
 
 
+def test_lognormal_regrid_inside_density_keeps_pressure():
+    """Lognormal set of 671,089 particles from the uniform h guess: some h
+    outgrow the first grid's top cells, so the density call regrids (the
+    store is permuted) and starts again. P, and through it every force,
+    must use each particle's own u after that (element by element against
+    the oracle, P included)."""
+    p = inputs.config(5, 0.01)
+    g = run_gpu(p)
+    assert g["stats"]["rebuilds"] >= 1, g["stats"]["rebuilds"]
+    s = run_oracle(p)
+    compare_density(g, s)
+    compare_force(g, s)
+    force_counts_close(g, s)
+
+
 def test_lattice_on_cell_faces_and_box_edge():
     """Lattice through the origin (particles on the box faces and on every
     top-cell face): uniform rho and h, forces zero up to FP32 round-off."""
