@@ -186,6 +186,8 @@ typedef struct {
   int64_t cache_density_groups; /* groups whose density ran on their stored neighbours */
   int64_t cache_force_groups;   /* groups whose force ran on the density's neighbours */
   int64_t cache_built_groups;   /* groups whose density searched anew and stored them */
+  int64_t cache_relist_warps;   /* warps on stored neighbours whose h or motion made them
+                                   rebuild their per-lane lists from the stored stage */
 } sph_stats_t;
 
 /* Default parameters: gamma = 5/3, n_ngb = 48, h_tol = 1e-6, max_iter = 30,

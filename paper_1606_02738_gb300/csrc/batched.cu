@@ -547,6 +547,9 @@ static_assert(kLaneD % 4 == 0 && kLaneF % 4 == 0, "lists are padded to multiples
 // exact zero to the FP32 force sums (the compensated sums skip it).
 constexpr float kFar = 1e18f;
 
+static_assert(sizeof(unsigned short) * kNW * kCandD >= 12 * 384,
+              "the density's cand space holds the task shifts while a cached stage loads");
+
 template <int NS>
 struct DensSmem {
   unsigned dmax_bits;                       // largest dpath of a reloaded stage (float bits)
@@ -871,15 +874,20 @@ struct DensAcc {
 // Reload a group's stored stage (neighbour cache) into shared memory at the
 // current positions: entry k of segment w (k < wc[w]) is particle sj[k],
 // moved into the group frame by its task's shift (the same sum as the
-// staging, so the same FP32 values). FORCE also stages (A', h^2) and the
-// index. Returns the stage range; *dmax receives the largest dpath of the
-// staged particles. Called by every thread of the block.
+// staging, so the same FP32 values). The group's task shifts are first
+// copied to `shift` (shared memory free at this point, >= 3 ntask floats),
+// then every thread takes 8 entries at a time with their loads in flight
+// together. FORCE also stages (A', h^2) and the index. Returns the stage
+// range; *dmax receives the largest dpath of the staged particles (through
+// *dmax_bits, shared). Called by every thread of the block.
 template <bool FORCE>
 __device__ StageRange load_stage_cached(const CacheArgs &C, int g, const int wc[4],
-                                        const Task *tasks, const float4 *pm, const float4 *fi,
-                                        float4 *sq, float2 *sf, int *sj, int cap,
-                                        unsigned *dmax_bits, float *dmax) {
-  __syncthreads();  // every warp is done with the previous group's stage
+                                        const Task *tasks, int ntask, const float4 *pm,
+                                        const float4 *fi, float4 *sq, float2 *sf, int *sj,
+                                        int cap, float *shift, unsigned *dmax_bits,
+                                        float *dmax) {
+  __syncthreads();  // every warp is done with the previous group's stage and shift space
+  if (threadIdx.x == 0) *dmax_bits = 0u;
   StageRange r;
   r.segcap = cap / kNW;
   r.pre1 = wc[0];
@@ -889,27 +897,58 @@ __device__ StageRange load_stage_cached(const CacheArgs &C, int g, const int wc[
   r.maxw = max(max(wc[0], wc[1]), max(wc[2], wc[3]));
   r.over = 0;
   r.unmapped = 0;
-  if (threadIdx.x == 0) *dmax_bits = 0u;
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    const Task tk = tasks[t];
+    shift[3 * t] = tk.sx;
+    shift[3 * t + 1] = tk.sy;
+    shift[3 * t + 2] = tk.sz;
+  }
   const size_t base = (size_t)g * C.ns;
-  float dm = 0.f;
+  constexpr int kU = 8;
+  const int t0 = threadIdx.x;
+  int k[kU], j[kU], sl[kU];
+  // the first 8 entries' indices load while the shifts are being written
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int t = t0 + u * blockDim.x;
+    k[u] = t < r.total ? r.index(t) : -1;
+    j[u] = k[u] >= 0 ? C.sj[base + k[u]] : 0;
+    sl[u] = k[u] >= 0 ? (int)C.slot[base + k[u]] : 0;
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < r.total; t += blockDim.x) {
-    const int k = r.index(t);
-    const int j = C.sj[base + k];
-    const Task tk = tasks[C.slot[base + k]];
-    const float4 p4 = pm[j];
-    float4 q = make_float4(tk.sx, tk.sy, tk.sz, 0.f);
-    q.x += p4.x;
-    q.y += p4.y;
-    q.z += p4.z;
-    q.w = p4.w;
-    sq[k] = q;
-    if (FORCE) {
-      const float4 f = fi[j];
-      sf[k] = make_float2(f.z, f.w);
-      sj[k] = j;
+  float dm = 0.f;
+  for (int tb = 0;; tb += kU * blockDim.x) {
+    float4 p4[kU], f4[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      p4[u] = pm[j[u]];
+      if (FORCE) f4[u] = fi[j[u]];
+      dm = fmaxf(dm, k[u] >= 0 ? C.dpath[j[u]] : 0.f);
     }
-    dm = fmaxf(dm, C.dpath[j]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (k[u] < 0) continue;
+      const float *sh = shift + 3 * sl[u];
+      float4 q = make_float4(sh[0], sh[1], sh[2], 0.f);
+      q.x += p4[u].x;
+      q.y += p4[u].y;
+      q.z += p4[u].z;
+      q.w = p4[u].w;
+      sq[k[u]] = q;
+      if (FORCE) {
+        sf[k[u]] = make_float2(f4[u].z, f4[u].w);
+        sj[k[u]] = j[u];
+      }
+    }
+    const int tn = tb + kU * blockDim.x;
+    if (tn >= r.total) break;  // block-uniform
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int t = tn + t0 + u * blockDim.x;
+      k[u] = t < r.total ? r.index(t) : -1;
+      j[u] = k[u] >= 0 ? C.sj[base + k[u]] : 0;
+      sl[u] = k[u] >= 0 ? (int)C.slot[base + k[u]] : 0;
+    }
   }
   dm = warp_max_f(dm);
   if ((threadIdx.x & 31) == 0) atomicMax(dmax_bits, __float_as_uint(dm));
@@ -918,10 +957,22 @@ __device__ StageRange load_stage_cached(const CacheArgs &C, int g, const int wc[
   return r;
 }
 
-// REUSE (first tier, neighbour cache): this instantiation runs the groups
-// whose stored stage is still valid (gmode[g] = 1) from that stage; the other
-// runs the rest, staging anew and storing the stage and lists. Two
-// instantiations keep each path's registers apart.
+// Asynchronous copy of `rows` rows of 32 list entries (64 bytes each) from
+// global to shared memory, 16 bytes per request (cp.async, no registers
+// held); wait with cp_async_wait_all().
+__device__ __forceinline__ void cp_async_rows(unsigned short *dst, const unsigned short *src,
+                                              int rows, int lane) {
+  for (int t = lane; t < rows * 4; t += 32) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst + 8 * t);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src + 8 * t)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 template <bool KAHAN, int NS, bool REUSE>
 __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     k_density_batched(BatchDensArgs a, int tier) {
@@ -936,7 +987,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   unsigned short *cand = S.cand[warp];
   unsigned short *list = S.list[warp];
   unsigned long long ntest = 0, inter = 0;
-  int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0}, n_built = 0;
+  int max_it = 0, st_bits = 0, stage_max = 0, n_direct[2] = {0, 0}, n_built = 0, n_relist = 0;
   if (threadIdx.x == 0) S.stage[NS] = make_float4(kFar, kFar, kFar, 0.f);  // read after a barrier
   // the neighbour cache: first tier only
   const bool use_cache = !TIGHT && a.cache_on;
@@ -973,8 +1024,17 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
       int wc[4];
       for (int w = 0; w < 4; ++w) wc[w] = M->wc[w];
       Rgb = M->Rg;
-      sr = load_stage_cached<false>(a.cache, g, wc, a.tasks + e0, a.pm, nullptr, S.stage,
-                                    nullptr, nullptr, NS, &S.dmax_bits, &Dst);
+      // this warp's stored lists start copying to shared memory now (the
+      // previous group's warps are done with them: the load's barrier
+      // follows, and each warp copies only its own rows)
+      const int tp = M->tpad[warp];
+      if (tp > 0)
+        cp_async_rows(S.list[warp],
+                      a.cache.list + ((size_t)g * kNW + warp) * a.cache.lane_cap * 32, tp, lane);
+      sr = load_stage_cached<false>(a.cache, g, wc, a.tasks + e0, min(nt, a.tcap), a.pm,
+                                    nullptr, S.stage, nullptr, nullptr, NS,
+                                    reinterpret_cast<float *>(&S.cand[0][0]), &S.dmax_bits,
+                                    &Dst);
     } else {
       sr = stage_group<false>(&a, nullptr, G, e0, e0 + min(nt, a.tcap), warp, lane, Rg, S.stage,
                               nullptr, nullptr, S.wcount, (unsigned char *)cand, NS,
@@ -1033,7 +1093,6 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     bool fresh = true;      // the per-lane lists were built in this call
     bool have_cand = true;  // cand holds the filtered stage (else a list rebuild refilters)
     if constexpr (REUSE) {
-      const size_t lrow = ((size_t)g * kNW + warp) * a.cache.lane_cap * 32;
       const float dp = has ? a.cache.dpath[i] : 0.f;
       const float delta = cell_motion(a.cache, B, G.cell, lane);
       float rw = has ? Rgb - dp - delta : 3e38f;
@@ -1041,7 +1100,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
       Rgw = rw;
       const int tp = M->tpad[warp];
       if (tp >= 0) {  // stored lists: complete within rl_i - dpath_i - D for staged j
-        for (int t = 0; t < tp; ++t) list[t * 32 + lane] = a.cache.list[lrow + t * 32 + lane];
+        cp_async_wait_all();
         __syncwarp();
         cnt = tp;
         tpad = tp;
@@ -1052,6 +1111,9 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
         need_list = false;
         // the stored lists serve only if every starting h lies within them
         need_filter = __any_sync(0xffffffffu, has && it.h > rl);
+        // motion (not a grown h) made them incomplete: counts toward a new epoch
+        const bool grown = __any_sync(0xffffffffu, has && it.h > a.cache.rl[i]);
+        if (need_filter && !grown && lane == 0) atomicAdd(&a.cache.ctl->lfail, 1);
       }
     }
     float4 fs = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1146,6 +1208,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
       if (__all_sync(0xffffffffu, fin)) break;
     }
     if (lane == 0 && mode) ++n_direct[mode - 1];
+    if (REUSE && fresh && lane == 0) ++n_relist;
     if (failed || !__all_sync(0xffffffffu, fin)) {
       // this warp's unfinished targets go to the third tier (done is not set)
       if (lane == 0) {
@@ -1200,6 +1263,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     if (n_direct[1]) atomicAdd(&a.ctr->direct[1], n_direct[1]);
   }
   if (n_built) atomicAdd(&a.ctr->cache_built, n_built);
+  if (n_relist) atomicAdd(&a.ctr->cache_relist, n_relist);
 }
 
 // One lane's force sums (Eqs. dvdt, dudt) over its share of the staged
@@ -1578,6 +1642,7 @@ __global__ void k_cache_init(CacheCtl *ctl, int n_groups) {
   ctl->build_all = 1;
   ctl->fail = 0;
   ctl->n_groups = n_groups;
+  ctl->lfail = 0;
 }
 
 void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s) {
@@ -1586,8 +1651,9 @@ void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s) {
 }
 
 __global__ void k_cache_decide(CacheCtl *ctl) {
-  ctl->build_all = ctl->fail * 8 > ctl->n_groups ? 1 : 0;
+  ctl->build_all = (ctl->fail * 8 > ctl->n_groups || ctl->lfail * 2 > ctl->n_groups) ? 1 : 0;
   ctl->fail = 0;
+  ctl->lfail = 0;
 }
 
 void launch_cache_decide(CacheCtl *ctl, cudaStream_t s) {
@@ -1868,6 +1934,8 @@ struct ForceReuseSmem {
 };
 
 constexpr int force_reuse_min_blocks(int nsd) { return nsd == kStageD ? 6 : 4; }
+static_assert(sizeof(unsigned) * kNW * kSub * ((kStageD + 32) / 32) >= 12 * 384,
+              "the force-on-cache bitmap space holds the task shifts while the stage loads");
 
 template <bool KAHAN, int NSD>
 __global__ void __launch_bounds__(kNW * 32, force_reuse_min_blocks(NSD))
@@ -1890,9 +1958,11 @@ __global__ void __launch_bounds__(kNW * 32, force_reuse_min_blocks(NSD))
     const GroupCache &M = C.meta[g];
     int wc[4];
     for (int w = 0; w < 4; ++w) wc[w] = M.wc[w];
+    const int ntask = min(C.tcount[g], a.tcap);
     float Dst;
-    const StageRange sr = load_stage_cached<true>(C, g, wc, C.tasks + (size_t)g * a.tcap, a.pm,
-                                                  a.fi, S.sq, S.sf, S.sj, NSD, &S.dmax_bits, &Dst);
+    const StageRange sr = load_stage_cached<true>(
+        C, g, wc, C.tasks + (size_t)g * a.tcap, ntask, a.pm, a.fi, S.sq, S.sf, S.sj, NSD,
+        reinterpret_cast<float *>(&S.bm[0][0][0]), &S.dmax_bits, &Dst);
     const int tloc = warp * kSub + (lane >> 2);
     const bool has = tloc < G.count;
     if (!__any_sync(0xffffffffu, has)) continue;
@@ -1916,14 +1986,14 @@ __global__ void __launch_bounds__(kNW * 32, force_reuse_min_blocks(NSD))
     const int tp = M.tpad[warp];
     const size_t lrow = ((size_t)g * kNW + warp) * C.lane_cap * 32;
     ForceAcc<KAHAN> acc;
-    // (a) listed entries (sentinel padded, x4)
-    for (int t = 0; t < tp; t += 4) {
-      int k[4];
+    // (a) listed entries (sentinel padded, x4), 8 rows per round trip
+    for (int t = 0; t < tp; t += 8) {
+      int k[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) k[u] = C.list[lrow + (t + u) * 32 + lane];
+      for (int u = 0; u < 8; ++u) k[u] = t + u < tp ? C.list[lrow + (t + u) * 32 + lane] : NSD;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!has) continue;
+      for (int u = 0; u < 8; ++u) {
+        if (!has || t + u >= tp) continue;
         if (k[u] < NSD) atomicOr(&bm[k[u] >> 5], 1u << (k[u] & 31));
         acc.add(S, k[u], a.vu, px, py, pz, fi, vi, fi.w, NSD);
       }

@@ -719,6 +719,7 @@ CacheArgs cache_args(sph_ctx *c) {
   a.fuse = as<unsigned char>(c->vc_fuse);
   a.ctl = as<CacheCtl>(c->vc_ctl);
   a.tasks = as<Task>(c->gd_tasks);
+  a.tcount = as<int>(c->gd_off);
   a.ns = cache_stage_slots(c->p.tile);
   a.lane_cap = cache_lane_cap(c->p.tile);
   return a;
@@ -1641,6 +1642,7 @@ int sph_stats(sph_ctx *c, sph_stats_t *out) {
   out->cache_density_groups = c->ctr_h->cache_used[0];
   out->cache_force_groups = c->ctr_h->cache_used[1];
   out->cache_built_groups = c->ctr_h->cache_built;
+  out->cache_relist_warps = c->ctr_h->cache_relist;
   out->kernel_launches = c->launches;  // before the extremes kernel below
   std::vector<double> hb;
   double hmin = 0, hmax = 0;

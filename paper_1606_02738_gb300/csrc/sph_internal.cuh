@@ -101,6 +101,7 @@ struct DevCounters {
   int cache_used[2];                  // groups whose density / force ran on the stored
                                       // neighbour cache (no walk, no staging tests)
   int cache_built;                    // groups whose density built (and stored) a new cache
+  int cache_relist;                   // warps on a stored stage that rebuilt their lists
   int step_status;                    // kErr* bits of the kicks and the grid check (last
                                       // field: the density's counter reset keeps it)
 };
@@ -598,9 +599,9 @@ static_assert(sizeof(GroupCache) == 64, "GroupCache layout");
 
 struct CacheCtl {
   int build_all;   // 1: the next density builds every group's cache (new epoch)
-  int fail;        // groups whose stored stage no longer covered their h (this call)
+  int fail;        // groups whose stored stage motion made incomplete (this call)
   int n_groups;
-  int pad;
+  int lfail;       // warps whose stored lists motion made incomplete (this call)
 };
 
 struct CacheArgs {
@@ -615,6 +616,7 @@ struct CacheArgs {
   unsigned char *fuse;     // [n_groups] 1: this force call reuses it
   CacheCtl *ctl;
   const Task *tasks;       // the density's task slots (the stored stage's shifts)
+  const int *tcount;       // the density's task count per group
   int ns;                  // stage slots per group (layout stride)
   int lane_cap;            // list entries per lane (layout stride)
 };
@@ -684,8 +686,9 @@ struct BatchDensArgs {
   CacheArgs cache;
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
-// The next call's epoch decision (one thread): a new epoch when more than an
-// eighth of the groups had to rebuild their cache in this call.
+// The next call's epoch decision (one thread): a new epoch when motion made
+// more than an eighth of the groups restage, or of the warps rebuild their
+// lists, in this call.
 void launch_cache_decide(CacheCtl *ctl, cudaStream_t s);
 // A new epoch: every group builds (and stores) its cache in the next density.
 void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s);

@@ -76,7 +76,8 @@ class sph_stats_t(ctypes.Structure):
                 ("sort_launches", ctypes.c_int64), ("reused_steps", ctypes.c_int64),
                 ("redone_steps", ctypes.c_int64), ("graph_steps", ctypes.c_int64),
                 ("n_groups", ctypes.c_int64), ("cache_density_groups", ctypes.c_int64),
-                ("cache_force_groups", ctypes.c_int64), ("cache_built_groups", ctypes.c_int64)]
+                ("cache_force_groups", ctypes.c_int64), ("cache_built_groups", ctypes.c_int64),
+                ("cache_relist_warps", ctypes.c_int64)]
 
 
 class SphError(RuntimeError):

@@ -52,7 +52,7 @@ def test_params_struct_matches_header_defaults(libpath):
     assert [f for f, _ in sph.sph_params._fields_][-6:] == ["profile", "pair_sort", "reuse_grid",
                                                            "tile", "cell_factor", "reuse_lists"]
     assert ctypes.sizeof(sph.sph_stats_t) == (10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 +
-                                              2 * 4 + 8 * 4 + 4 * 8 + 4 * 8)
+                                              2 * 4 + 8 * 4 + 4 * 8 + 5 * 8)
 
 
 def test_param_pair_sort_validated(libpath):
