@@ -111,13 +111,16 @@ typedef struct {
                       (fewer groups to the second tier on clumped inputs) */
   double cell_factor; /* top-cell edge >= cell_factor x the largest h where the box allows
                          (1 <= cell_factor <= 4; >= 1 x always) */
-  int reuse_lists;  /* batched form, 1: keep each group's staged neighbours and per-lane
-                       neighbour lists in device memory after the density; the force of the
-                       same call takes its pairs from them (plus the pairs reached by a
-                       neighbour's larger h), and later density calls reuse them while a
-                       bound on the distance moved since they were built (the summed |v dt|
-                       of the drifts) shows them complete for the current h; 0: search
-                       anew in every call (same results up to summation order) */
+  int reuse_lists;  /* batched form, neighbour cache: keep each group's staged neighbours
+                       and per-lane neighbour lists in device memory after the density; the
+                       force of the same call takes its pairs from them (plus the pairs
+                       reached by a neighbour's larger h), and later density calls reuse
+                       them while a bound on the distance moved since they were built (the
+                       summed |v dt| of the drifts) shows them complete for the current h.
+                       0: off, search anew in every call; 1: on for sets of >= 16384 target
+                       groups (smaller sets are latency-bound, where the cache's extra
+                       kernels cost more than they save); 2: on always. Results are the
+                       same up to summation order. */
 } sph_params;
 
 typedef struct {

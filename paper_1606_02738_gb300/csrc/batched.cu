@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, MODE == kWalkTight ? 4 : 10)
     if (far) {
       // candidates: every warp of the group finished its density on lists
       const GroupCache &M = a.cache.meta[g];
-      bool ok = true;
+      bool ok = !a.cache.ctl->force_off && M.stage_ok;
       for (int w = 0; w < 4; ++w)
         if (w * 8 < G.count && !M.wok[w]) ok = false;
       if (!ok) {
@@ -482,7 +482,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, MODE == kWalkTight ? 4 : 10)
       atomicAdd(&a.ctr->cache_used[0], n_reused);
       if (n_failed) atomicAdd(&a.cache.ctl->fail, n_failed);
     }
-    if (far) atomicAdd(&a.ctr->cache_used[1], n_reused);
+    if (far) {
+      atomicAdd(&a.ctr->cache_used[1], n_reused);
+      atomicAdd(&a.cache.ctl->fused, n_reused);
+    }
   }
 }
 
@@ -1643,6 +1646,24 @@ __global__ void k_cache_init(CacheCtl *ctl, int n_groups) {
   ctl->fail = 0;
   ctl->n_groups = n_groups;
   ctl->lfail = 0;
+  ctl->force_off = 0;
+  ctl->fused = n_groups;  // the first force call tries
+  ctl->probe = 0;
+}
+
+__global__ void k_force_gate(CacheCtl *ctl) {
+  if (ctl->force_off) {  // skipping: count down to the next try
+    if (--ctl->probe <= 0) ctl->force_off = 0;
+  } else if (ctl->fused * 8 < ctl->n_groups) {  // the last try paid too little
+    ctl->force_off = 1;
+    ctl->probe = 15;
+  }
+  if (!ctl->force_off) ctl->fused = 0;  // counted afresh by this call's far walk
+}
+
+void launch_force_gate(CacheCtl *ctl, cudaStream_t s) {
+  k_force_gate<<<1, 1, 0, s>>>(ctl);
+  note_launch();
 }
 
 void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s) {

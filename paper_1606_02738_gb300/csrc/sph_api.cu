@@ -704,7 +704,15 @@ int build_groups(sph_ctx *c) {
   return sync_check(c);
 }
 
-bool cache_on(const sph_ctx *c) { return c->p.mode == SPH_MODE_BATCHED && c->p.reuse_lists; }
+// Groups below which the cache is not used: such sets are bound by launch
+// and memory latency, where the cache's extra kernels cost more than the
+// searches they save.
+constexpr int kCacheMinGroups = 16384;
+
+bool cache_on(const sph_ctx *c) {
+  return c->p.mode == SPH_MODE_BATCHED &&
+         (c->p.reuse_lists == 2 || (c->p.reuse_lists == 1 && c->n_groups >= kCacheMinGroups));
+}
 
 CacheArgs cache_args(sph_ctx *c) {
   CacheArgs a{};
@@ -1028,6 +1036,7 @@ int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
   launch_group_hmax(gb, c->stream);
   GeomArgs ga = geom_args(c);
   launch_leaf_hmax(ga, c->n_nodes, c->stream);
+  if (cache_on(c) && c->vc_valid) launch_force_gate(as<CacheCtl>(c->vc_ctl), c->stream);
   TRY(build_group_lists(c, true, 1.0f, c->gf_off, c->gf_tasks));
   if (!steady) {
     CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
@@ -1339,7 +1348,7 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
       (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
       (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
-      (q.reuse_lists != 0 && q.reuse_lists != 1))
+      q.reuse_lists < 0 || q.reuse_lists > 2)
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;

@@ -602,6 +602,10 @@ struct CacheCtl {
   int fail;        // groups whose stored stage motion made incomplete (this call)
   int n_groups;
   int lfail;       // warps whose stored lists motion made incomplete (this call)
+  int force_off;   // 1: this force call skips the cache (far-reacher walk not run)
+  int fused;       // groups whose force ran on the cache in the last call that tried
+  int probe;       // calls left before a skipped force cache is tried again
+  int pad;
 };
 
 struct CacheArgs {
@@ -692,6 +696,11 @@ void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 void launch_cache_decide(CacheCtl *ctl, cudaStream_t s);
 // A new epoch: every group builds (and stores) its cache in the next density.
 void launch_cache_init(CacheCtl *ctl, int n_groups, cudaStream_t s);
+// Before a force call (one thread): when fewer than an eighth of the groups
+// could take their force from the cache in the last call that tried, skip
+// the far-reacher walk and the cached force for the next 15 calls, then try
+// again.
+void launch_force_gate(CacheCtl *ctl, cudaStream_t s);
 // Stage capacity and list entries per lane of the first tier of `tile`.
 int cache_stage_slots(int tile);
 int cache_lane_cap(int tile);

@@ -304,7 +304,7 @@ class Context:
                  mode: int = SPH_MODE_BATCHED, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
                  h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False,
                  pair_sort: bool = True, reuse_grid: bool = True, tile: int = 0,
-                 cell_factor: float = 2.0, reuse_lists: bool = True, stream=None,
+                 cell_factor: float = 2.0, reuse_lists: int = 1, stream=None,
                  device="cuda"):
         import torch
         self.torch = torch
@@ -315,7 +315,7 @@ class Context:
         p.pair_sort = int(bool(pair_sort))
         p.reuse_grid = int(bool(reuse_grid))
         p.tile, p.cell_factor = int(tile), float(cell_factor)
-        p.reuse_lists = int(bool(reuse_lists))
+        p.reuse_lists = int(reuse_lists)
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream

@@ -1,4 +1,5 @@
-"""The batched form's neighbour cache (reuse_lists = 1), through the C ABI and
+"""The batched form's neighbour cache (reuse_lists = 2: on whatever the set's
+size), through the C ABI and
 against the FP64 oracle. The density stores each group's staged neighbours
 and per-lane lists; the force of the same call takes its pairs from them
 (plus the pairs a neighbour's larger h adds), and later density calls reuse
@@ -50,7 +51,7 @@ def test_later_calls_reuse_density_and_force(tile, precision):
     clustered roots) builds every group's cache; later calls on the same
     positions and the converged h run most groups' density and force on it."""
     p = inputs.clustered(30011, n_spheres=8, seed=81, sigma_v=0.2)
-    c = sph.Context(tile=tile, precision=precision).load(p)
+    c = sph.Context(tile=tile, precision=precision, reuse_lists=2).load(p)
     c.density()
     c.force()
     st1 = c.stats()
@@ -66,9 +67,9 @@ def test_later_calls_reuse_density_and_force(tile, precision):
     g = {k: c.get(k).cpu().numpy() for k in FIELDS}
     c.close()
     assert st["cache_density_groups"] > 0.5 * st["n_groups"], st["cache_density_groups"]
-    # clumps put particles of large h beside most groups: those take the full
-    # force path, the rest the cache
-    assert st["cache_force_groups"] > 0, st["cache_force_groups"]
+    # clumps put particles of large h beside most groups, which then take the
+    # full force path (and the cached force is skipped while it would serve
+    # fewer than an eighth of the groups); the results do not depend on it
     s = run_oracle(p)
     compare_density(g, s)
     compare_force(g, s)
@@ -84,14 +85,14 @@ def test_sod_steps_reuse_the_cache_and_match_oracle(tile, precision):
     oracle as closely as without the cache."""
     p = inputs.sod(nx_left=96, n_yz_left=24, nx_right=48, n_yz_right=12)
     dt, n = 2e-3, 6
-    g = _steps(p, n, dt, tile=tile, precision=precision)
+    g = _steps(p, n, dt, tile=tile, precision=precision, reuse_lists=2)
     last = g["stats"]
     assert last["cache_density_groups"] > 0.5 * last["n_groups"], last["cache_density_groups"]
     assert last["cache_force_groups"] > 0.5 * last["n_groups"], last["cache_force_groups"]
     s = run_oracle(p, steps=n, dt=dt)
     compare_density(g, s, tol_rho=2e-5, tol_h=2e-5, counts=False, check_P=False)
     compare_force(g, s, tol_a=3e-4, tol_du=3e-4)
-    g0 = _steps(p, n, dt, tile=tile, precision=precision, reuse_lists=False)
+    g0 = _steps(p, n, dt, tile=tile, precision=precision, reuse_lists=0)
     assert g0["stats"]["cache_built_groups"] == 0 and g0["stats"]["cache_force_groups"] == 0
     # the two forms sum in different orders: forces within 1e-4 max|a| of each
     # other move x apart by at most n^2 dt^2 1e-4 max|a|
@@ -109,7 +110,7 @@ def test_fast_motion_rebuilds_groups_and_still_matches_oracle():
     p = inputs.uniform(20000, seed=403, sigma_v=1.5)
     p.u = np.full(p.n, 10.0, dtype=np.float32)  # sound speed 3.3: a subsonic flow
     dt, n = 1.5e-3, 6
-    g = _steps(p, n, dt)
+    g = _steps(p, n, dt, reuse_lists=2)
     built_later = sum(h["cache_built_groups"] for h in g["hist"][2:])
     assert built_later > 0, [h["cache_built_groups"] for h in g["hist"]]
     s = run_oracle(p, steps=n, dt=dt)
@@ -137,7 +138,7 @@ def test_large_h_next_to_small_h_takes_the_full_force_path():
     p = inputs.uniform(x.shape[0], seed=404, sigma_v=0.2)
     p.x = np.mod(x, 1.0)
     p.h = np.full(p.n, 2.5 * a)
-    c = sph.Context().load(p)
+    c = sph.Context(reuse_lists=2).load(p)
     c.density()
     c.force()
     c.density()
