@@ -121,6 +121,15 @@ typedef struct {
                        groups (smaller sets are latency-bound, where the cache's extra
                        kernels cost more than they save); 2: on always. Results are the
                        same up to summation order. */
+  int work_queue;   /* batched form (Section 3.2, task queue and costs): how the
+                       first-tier kernels share the target groups out among their
+                       blocks. 0: a fixed grid stride. 1 (default): as 2 for sets of
+                       >= 2^20 groups, else as 0. 2: every block claims 32 groups at a
+                       time from a queue in group order until it is empty (neighbouring
+                       groups stay together in time). 3: the same queue in measured
+                       cost order: chunks of 32 groups, costliest first, a group's cost
+                       being its duration in the last call (first: target count x task
+                       count). Results are identical in every mode. */
 } sph_params;
 
 typedef struct {

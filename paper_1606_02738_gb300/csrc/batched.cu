@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -562,6 +564,7 @@ struct DensSmem {
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][dens_lane(NS) * 32];  // [entry][lane]
   int wcount[kNW];
+  int qslot[4];                             // work queue: claimed chunks (two slots)
 };
 
 template <int NS>
@@ -573,6 +576,7 @@ struct ForceSmem {
   unsigned short cand[kNW][force_cand(NS)];
   unsigned short list[kNW][force_lane(NS) * 32];
   int wcount[kNW];
+  int qslot[4];                             // work queue: claimed chunks (two slots)
 };
 
 // Group g of a launch: tier 0 walks every group; tier 1 walks the groups
@@ -584,6 +588,80 @@ __device__ __forceinline__ int tier_group(int tier, int q, const int *queue) {
 __device__ __forceinline__ int tier_count(int tier, int n_groups, const int *queued) {
   return tier == 0 ? n_groups : *queued;
 }
+
+// The block-uniform cursor of a first-tier group loop. With a work queue,
+// warp 0 claims the next kClaim queue positions with one atomic (claiming
+// again while every group of the claim is one this launch skips) and hands
+// the groups to run over as a bit mask through two alternating shared slots
+// (a slot is rewritten only two claims later, behind a barrier that every
+// thread reaches after reading it); without, a grid stride. Thread 0 times
+// each group run (from its fetch to the next fetch) into wq.cost.
+constexpr int kClaim = 32;
+// Queue positions of n groups: whole chunks when ordered by chunk.
+__device__ __forceinline__ int queue_positions(const WorkQueue &wq, int n) {
+  return wq.order ? (n + kClaim - 1) / kClaim * kClaim : n;
+}
+struct GroupCursor {
+  bool dyn;
+  int it;
+  int base;        // queue position of the claimed chunk
+  unsigned mask;   // its groups still to run
+  int g;           // thread 0: the group being timed, or -1
+  long long t0;
+  template <class Skip>
+  __device__ int fetch(const WorkQueue &wq, int *slot, int ng, Skip skip) {
+    if (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      return base + b;
+    }
+    int *s = slot + 2 * (it++ & 1);
+    if (threadIdx.x < 32) {
+      int b0;
+      unsigned m;
+      do {
+        b0 = 0;
+        if (threadIdx.x == 0) b0 = atomicAdd(wq.head, kClaim);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        const int p = b0 + (int)threadIdx.x;
+        const int gp = p < ng ? (wq.order ? wq.order[p] : p) : -1;  // -1: past the last group
+        const bool run = gp >= 0 && !skip(gp);
+        m = __ballot_sync(0xffffffffu, run);
+      } while (m == 0u && b0 < ng);
+      if (threadIdx.x == 0) {
+        s[0] = b0;
+        s[1] = (int)m;
+      }
+    }
+    __syncthreads();
+    base = s[0];
+    mask = (unsigned)s[1];
+    if (!mask) return ng;  // the queue is empty
+    const int b = __ffs(mask) - 1;
+    mask &= mask - 1;
+    return base + b;
+  }
+  template <class Skip>
+  __device__ int first(const WorkQueue &wq, int *slot, int ng, Skip skip) {
+    g = -1;
+    it = 0;
+    mask = 0u;
+    return dyn ? fetch(wq, slot, ng, skip) : (int)blockIdx.x;
+  }
+  template <class Skip>
+  __device__ int next(const WorkQueue &wq, int *slot, int ng, int q, Skip skip) {
+    if (!dyn) return q + gridDim.x;
+    if (threadIdx.x == 0 && g >= 0) wq.cost[g] = (float)(clock64() - t0);
+    g = -1;
+    return fetch(wq, slot, ng, skip);
+  }
+  __device__ void run(int group) {
+    if (dyn && threadIdx.x == 0) {
+      g = group;
+      t0 = clock64();
+    }
+  }
+};
 
 // The stage is laid out in kNW segments of cap / kNW entries, warp w's staged
 // particles in segment w in the order that warp found them (deterministic).
@@ -996,20 +1074,25 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   const bool use_cache = !TIGHT && a.cache_on;
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
-  for (int q = blockIdx.x; q < ng; q += gridDim.x) {
-    const int g = tier_group(tier, q, a.queue);
+  GroupCursor cur;
+  cur.dyn = tier == 0 && a.wq.head != nullptr;
+  const WorkQueue wq = {a.wq.order, cur.dyn ? a.wq.head + (REUSE ? 0 : 1) : nullptr, a.wq.cost};
+  const auto skip = [&](int g) { return use_cache && (a.cache.gmode[g] != 0) != REUSE; };
+  const int qn = cur.dyn ? queue_positions(wq, ng) : ng;
+  for (int q = cur.first(wq, S.qslot, qn, skip); q < qn; q = cur.next(wq, S.qslot, qn, q, skip)) {
+    const int g = cur.dyn ? (wq.order ? wq.order[q] : q) : tier_group(tier, q, a.queue);
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
     const float hcap = (float)B.hcap;
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
     if (use_cache && (a.cache.gmode[g] != 0) != REUSE) continue;  // the other instantiation's
+    cur.run(g);
     // tasks from the tight walk: complete only within each target's own
     // starting radius (block-uniform; a reused stage never came from one)
     const bool tightw = !REUSE && !TIGHT && a.wmode && a.wmode[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
-    constexpr bool reuse = REUSE;
     GroupCache *M = use_cache ? &a.cache.meta[g] : nullptr;
     float Rgb = Rg, Dst = 0.f;   // stage radius at the build, largest staged dpath
     if (TIGHT) __syncthreads();  // the previous group's warps are done reading tgt
@@ -1620,15 +1703,133 @@ __global__ void __launch_bounds__(kSWarps * 32) k_force_stream(BatchForceArgs a)
   }
 }
 
+// ---------------------------------------------------- task cost ordering
+//
+// The queue is ordered by chunks of kClaim consecutive groups (one claim
+// each), so that a block still runs neighbouring groups one after another
+// (their stages overlap in L1) while the chunks go costliest first.
+
+__device__ __forceinline__ float group_cost(const Group *groups, const int *tcount,
+                                            const float *cost, int g) {
+  const float c = cost[g];
+  return c > 0.f ? c : 64.f * (float)groups[g].count * (float)max(tcount[g], 1);
+}
+
+// c > 0: its bits order like an unsigned integer; exponent and the top three
+// mantissa bits give eight bins per octave, the costliest first.
+__device__ __forceinline__ int cost_bin(float c) {
+  const unsigned k = min(__float_as_uint(c) >> 20, (unsigned)(kCostBins - 1));
+  return kCostBins - 1 - (int)k;
+}
+
+// One warp per chunk: its summed cost's bin into cbin[chunk] and the
+// histogram.
+__global__ void k_chunk_cost(const Group *groups, int n, const int *tcount, const float *cost,
+                             int *cbin, int *bins) {
+  __shared__ int h[kCostBins];
+  for (int b = threadIdx.x; b < kCostBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = (n + kClaim - 1) / kClaim;
+  for (int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < n_chunks;
+       ch += (gridDim.x * blockDim.x) >> 5) {
+    const int g = ch * kClaim + lane;
+    float c = g < n ? group_cost(groups, tcount, cost, g) : 0.f;
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      const int b = cost_bin(fmaxf(c, 1.f));
+      cbin[ch] = b;
+      atomicAdd(&h[b], 1);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kCostBins; b += blockDim.x)
+    if (h[b]) atomicAdd(&bins[b], h[b]);
+}
+
+// One block of kCostBins / 2 threads: bins become their exclusive prefix
+// sums (the first queue chunk of each bin); the queue heads are zeroed.
+__global__ void k_cost_scan(int *bins, int *heads, int n_heads) {
+  __shared__ int wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int v0 = bins[2 * t], v1 = bins[2 * t + 1];
+  int incl = v0 + v1;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;  // inclusive over the warps
+  }
+  __syncthreads();
+  const int ex = incl - v0 - v1 + (warp ? wsum[warp - 1] : 0);
+  bins[2 * t] = ex;
+  bins[2 * t + 1] = ex + v0;
+  if (t < n_heads) heads[t] = 0;
+}
+
+// One warp per chunk: the chunk takes its bin's next queue chunk and lays
+// its groups out there (-1 past the last group).
+__global__ void k_chunk_scatter(int n, const int *cbin, int *bins, int *order) {
+  const int lane = threadIdx.x & 31;
+  const int n_chunks = (n + kClaim - 1) / kClaim;
+  for (int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < n_chunks;
+       ch += (gridDim.x * blockDim.x) >> 5) {
+    int pos = 0;
+    if (lane == 0) pos = atomicAdd(&bins[cbin[ch]], 1);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    const int g = ch * kClaim + lane;
+    order[pos * kClaim + lane] = g < n ? g : -1;
+  }
+}
+
+void launch_cost_order(const Group *groups, int n_groups, const int *tcount, const float *cost,
+                       int *order, int *bins, int *cbin, int *heads, int n_heads,
+                       cudaStream_t s) {
+  static_assert(kCostBins == 2048, "k_cost_scan holds two bins per thread of one block");
+  static_assert(kClaim == 32, "a chunk is one warp's lanes");
+  if (n_groups <= 0) return;
+  cudaMemsetAsync(bins, 0, sizeof(int) * kCostBins, s);
+  const int n_chunks = (n_groups + kClaim - 1) / kClaim;
+  const int blocks = std::min((n_chunks + 7) / 8, 152 * 8);
+  k_chunk_cost<<<blocks, 256, 0, s>>>(groups, n_groups, tcount, cost, cbin, bins);
+  note_launch();
+  k_cost_scan<<<1, kCostBins / 2, 0, s>>>(bins, heads, n_heads);
+  note_launch();
+  k_chunk_scatter<<<blocks, 256, 0, s>>>(n_groups, cbin, bins, order);
+  note_launch();
+}
+
+// Blocks of `kernel` resident on the whole GPU at once (the grid of a
+// launch that claims its groups from a work queue).
+template <class K>
+int resident_blocks(K kernel, int bytes) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kNW * 32, bytes);
+  return std::max(per, 1) * std::max(sms, 1);
+}
+
 template <bool KAHAN, int NS, bool REUSE = false>
 void launch_density_tier(const BatchDensArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
+  static int resident = 0;
   const int bytes = (int)sizeof(DensSmem<NS>);
   if (!attr) {
     cudaFuncSetAttribute(k_density_batched<KAHAN, NS, REUSE>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    resident = resident_blocks(k_density_batched<KAHAN, NS, REUSE>, bytes);
     attr = true;
   }
+  if (tier == 0 && a.wq.head) blocks = std::min(a.n_groups, resident);
   k_density_batched<KAHAN, NS, REUSE><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
 }
@@ -1732,9 +1933,15 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   }
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
-  for (int q = blockIdx.x; q < ng; q += gridDim.x) {
-    const int g = tier_group(tier, q, a.queue);
+  GroupCursor cur;
+  cur.dyn = tier == 0 && a.wq.head != nullptr;
+  const auto skip = [&](int g) { return tier == 0 && a.cache_on && a.cache.fuse[g]; };
+  const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
+  for (int q = cur.first(a.wq, S.qslot, qn, skip); q < qn;
+       q = cur.next(a.wq, S.qslot, qn, q, skip)) {
+    const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
     if (tier == 0 && a.cache_on && a.cache.fuse[g]) continue;  // done on the cache
+    cur.run(g);
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
@@ -2080,12 +2287,15 @@ void launch_force_reuse(const BatchForceArgs &a, int blocks, cudaStream_t s) {
 template <bool KAHAN, int NS>
 void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
+  static int resident = 0;
   const int bytes = (int)sizeof(ForceSmem<NS>);
   if (!attr) {
     cudaFuncSetAttribute(k_force_batched<KAHAN, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          bytes);
+    resident = resident_blocks(k_force_batched<KAHAN, NS>, bytes);
     attr = true;
   }
+  if (tier == 0 && a.wq.head) blocks = std::min(a.n_groups, resident);
   k_force_batched<KAHAN, NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
 }

@@ -78,6 +78,9 @@ struct sph_ctx {
   // growable, library-owned
   // batched form: target groups and their task lists
   DevBuf gcount, groups, gd_off, gd_tasks, gf_off, gf_tasks, gqueue, lflag, gwmode;
+  // task cost ordering: measured cost per group (density, force), the order
+  // of the next first-tier launch, its bins and queue heads
+  DevBuf gcost_d, gcost_f, gorder, gbins, gcbin;
   int n_groups = 0;
   bool groups_valid = false;
   int64_t n_gd_tasks = 0, n_gf_tasks = 0;
@@ -695,6 +698,15 @@ int build_groups(sph_ctx *c) {
   c->n_groups = ng;
   TRY(ensure(c, c->groups, sizeof(Group) * (size_t)std::max(ng, 1)));
   TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1) * 5));  // queue, queue2
+  // new groups: no measured cost yet (the first order is the estimate)
+  TRY(ensure(c, c->gcost_d, sizeof(float) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, c->gcost_f, sizeof(float) * (size_t)std::max(ng, 1)));
+  const size_t n_chunks = (size_t)std::max(ng, 1) / 32 + 1;
+  TRY(ensure(c, c->gorder, sizeof(int) * n_chunks * 32));
+  TRY(ensure(c, c->gbins, sizeof(int) * (kCostBins + 4)));
+  TRY(ensure(c, c->gcbin, sizeof(int) * n_chunks));
+  CUDA_TRY(cudaMemsetAsync(c->gcost_d.p, 0, sizeof(float) * (size_t)std::max(ng, 1), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->gcost_f.p, 0, sizeof(float) * (size_t)std::max(ng, 1), c->stream));
   ga = group_args(c);
   launch_group_fill(ga, c->stream);
   launch_group_geometry(ga, c->stream);
@@ -840,6 +852,37 @@ const float4 *vu_of(const sph_ctx *c, VuSel sel) {
   return sel == kVuPredicted ? c->st.vu_pred : c->st.vu;
 }
 
+// Groups from which the first tier claims its groups from a work queue
+// (work_queue = 1): at least 32 claims of 32 groups for every block the
+// GPU holds at once. Below that a claim is a large share of a block's work
+// and the fixed grid stride balances as well.
+constexpr int kQueueMinGroups = 1 << 20;
+
+// 0: grid stride; 1: work queue in group order; 2: work queue in measured
+// cost order.
+int queue_mode(const sph_ctx *c) {
+  switch (c->p.work_queue) {
+    case 1: return c->n_groups >= kQueueMinGroups ? 1 : 0;
+    case 2: return 1;
+    case 3: return 2;
+    default: return 0;
+  }
+}
+
+// The work queue of a first-tier launch: heads [head0, head0 + n_heads) of
+// gbins; in cost order, ordered from the costs the last call measured.
+void work_queue(sph_ctx *c, const int *tcount, float *cost, int head0, int n_heads,
+                WorkQueue &wq) {
+  int *heads = as<int>(c->gbins) + kCostBins + head0;
+  const int mode = queue_mode(c);
+  if (mode == 2)
+    launch_cost_order(as<Group>(c->groups), c->n_groups, tcount, cost, as<int>(c->gorder),
+                      as<int>(c->gbins), as<int>(c->gcbin), heads, n_heads, c->stream);
+  else
+    cudaMemsetAsync(heads, 0, sizeof(int) * n_heads, c->stream);
+  wq = WorkQueue{mode == 2 ? as<int>(c->gorder) : nullptr, heads, cost};
+}
+
 int enqueue_density_batched(sph_ctx *c, VuSel vu_for_P, bool hmax_current = false) {
   if (!c->groups_valid) TRY(build_groups(c));
   TRY(cache_prepare(c));
@@ -888,6 +931,8 @@ int enqueue_density_batched(sph_ctx *c, VuSel vu_for_P, bool hmax_current = fals
   da.wmode = as<unsigned char>(c->gwmode);
   da.cache_on = cache_on(c) && c->vc_valid;
   if (da.cache_on) da.cache = cache_args(c);
+  // heads [0], [1]: the first-tier launches on stored stages and anew
+  if (queue_mode(c)) work_queue(c, as<int>(c->gd_off), as<float>(c->gcost_d), 0, 2, da.wq);
   tic(c, kDens);
   launch_density_batched(da, c->stream);
   toc(c, kDens);
@@ -1070,6 +1115,7 @@ int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
   fa.cache_on = cache_on(c) && c->vc_valid;
   if (fa.cache_on) fa.cache = cache_args(c);
+  if (queue_mode(c)) work_queue(c, as<int>(c->gf_off), as<float>(c->gcost_f), 2, 1, fa.wq);
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -1334,6 +1380,7 @@ void sph_default_params(sph_params *p) {
   p->tile = 0;
   p->cell_factor = 2.0;
   p->reuse_lists = 1;
+  p->work_queue = 1;
 }
 
 int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
@@ -1348,7 +1395,7 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
       (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
       (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
-      q.reuse_lists < 0 || q.reuse_lists > 2)
+      q.reuse_lists < 0 || q.reuse_lists > 2 || q.work_queue < 0 || q.work_queue > 3)
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
   if (!c) return SPH_ENOMEM;
@@ -1670,7 +1717,9 @@ void sph_destroy(sph_ctx *c) {
                     &c->frontier2,  &c->leaves,     &c->scan_tmp, &c->active,     &c->dens_off,
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
                     &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
-                    &c->gqueue,     &c->lflag,      &c->gwmode,   &c->vc_meta,    &c->vc_sj,
+                    &c->gqueue,     &c->lflag,      &c->gwmode,   &c->gcost_d,    &c->gcost_f,
+                    &c->gorder,     &c->gbins,      &c->gcbin,      &c->vc_meta,
+                    &c->vc_sj,
                     &c->vc_slot,    &c->vc_list,    &c->vc_rl,    &c->vc_dpath,   &c->vc_dmax,
                     &c->vc_gmode,   &c->vc_fuse,    &c->vc_ctl};
   for (DevBuf *b : bufs) release(*b);

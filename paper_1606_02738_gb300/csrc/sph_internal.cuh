@@ -654,6 +654,27 @@ struct GroupListArgs {
 constexpr int kWalkMaxNodes = 1 << 26;
 void launch_group_lists(const GroupListArgs &a, cudaStream_t s);
 
+// Work queue of a first-tier launch (task cost ordering, Section 3.2): the
+// blocks claim the groups kClaim queue positions at a time through *head,
+// in the order `order` gives (null: group order; -1 entries: no group).
+// The block that ran group g writes its duration to cost[g] (SM clock
+// cycles, from the group's fetch to the block's next fetch), which orders
+// the next call. head == nullptr: a static grid stride over the groups.
+struct WorkQueue {
+  const int *order;
+  int *head;
+  float *cost;
+};
+constexpr int kCostBins = 2048;   // cost buckets: 8 per octave
+// The queue order: chunks of 32 consecutive groups, costliest first (a
+// group's cost: cost[g] where measured, > 0, else the estimate count x
+// tasks from its walk), each chunk's groups in group order. order:
+// ceil(n_groups / 32) * 32 ints; bins: kCostBins ints; cbin:
+// ceil(n_groups / 32) ints. The n_heads queue heads are zeroed.
+void launch_cost_order(const Group *groups, int n_groups, const int *tcount, const float *cost,
+                       int *order, int *bins, int *cbin, int *heads, int n_heads,
+                       cudaStream_t s);
+
 struct BatchDensArgs {
   int n_groups;
   const Group *groups;
@@ -688,6 +709,9 @@ struct BatchDensArgs {
   const unsigned char *wmode;
   int cache_on;
   CacheArgs cache;
+  // first tier: the work queue (heads: [0] the launch on stored stages,
+  // [1] the launch that stages anew)
+  WorkQueue wq;
 };
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s);
 // The next call's epoch decision (one thread): a new epoch when motion made
@@ -729,6 +753,7 @@ struct BatchForceArgs {
   int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
   int cache_on;
   CacheArgs cache;
+  WorkQueue wq;          // first tier: the work queue
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
 

@@ -48,7 +48,7 @@ class sph_params(ctypes.Structure):
                 ("mode", ctypes.c_int), ("profile", ctypes.c_int),
                 ("pair_sort", ctypes.c_int), ("reuse_grid", ctypes.c_int),
                 ("tile", ctypes.c_int), ("cell_factor", ctypes.c_double),
-                ("reuse_lists", ctypes.c_int)]
+                ("reuse_lists", ctypes.c_int), ("work_queue", ctypes.c_int)]
 
 
 class sph_stats_t(ctypes.Structure):
@@ -304,8 +304,8 @@ class Context:
                  mode: int = SPH_MODE_BATCHED, n_ngb: float = 48.0, gamma: float = 5.0 / 3.0,
                  h_tol: float = 1e-6, max_iter: int = 30, profile: bool = False,
                  pair_sort: bool = True, reuse_grid: bool = True, tile: int = 0,
-                 cell_factor: float = 2.0, reuse_lists: int = 1, stream=None,
-                 device="cuda"):
+                 cell_factor: float = 2.0, reuse_lists: int = 1, work_queue: int = 1,
+                 stream=None, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -316,6 +316,7 @@ class Context:
         p.reuse_grid = int(bool(reuse_grid))
         p.tile, p.cell_factor = int(tile), float(cell_factor)
         p.reuse_lists = int(reuse_lists)
+        p.work_queue = int(work_queue)
         p.n_ngb, p.gamma, p.h_tol, p.max_iter = n_ngb, gamma, h_tol, max_iter
         self.params = p
         self.stream = stream

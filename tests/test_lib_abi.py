@@ -47,18 +47,21 @@ def test_params_struct_matches_header_defaults(libpath):
     assert p.n_ngb == 48.0 and p.h_tol == 1e-6 and p.max_iter == 30 and p.n_split == 64
     assert p.mode == sph.SPH_MODE_BATCHED and p.precision == sph.SPH_PREC_FP32
     assert p.pair_sort == 1 and p.profile == 0 and p.reuse_grid == 1
-    assert p.tile == 0 and p.cell_factor == 2.0 and p.reuse_lists == 1
-    assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4 + 8 + 8
-    assert [f for f, _ in sph.sph_params._fields_][-6:] == ["profile", "pair_sort", "reuse_grid",
-                                                           "tile", "cell_factor", "reuse_lists"]
+    assert p.tile == 0 and p.cell_factor == 2.0 and p.reuse_lists == 1 and p.work_queue == 1
+    assert ctypes.sizeof(sph.sph_params) == 3 * 8 + 8 * 4 + 8 + 2 * 4
+    assert [f for f, _ in sph.sph_params._fields_][-7:] == ["profile", "pair_sort", "reuse_grid",
+                                                           "tile", "cell_factor", "reuse_lists",
+                                                           "work_queue"]
     assert ctypes.sizeof(sph.sph_stats_t) == (10 * 8 + 4 * 4 + 2 * 8 + 2 * 4 + 5 * 8 + 7 * 8 +
                                               2 * 4 + 8 * 4 + 4 * 8 + 5 * 8)
 
 
-def test_param_pair_sort_validated(libpath):
+@pytest.mark.parametrize("field,value", [("pair_sort", 2), ("reuse_lists", 3), ("work_queue", 4),
+                                         ("work_queue", -1)])
+def test_param_switches_validated(libpath, field, value):
     L = sph.lib()
     bad = sph.sph_default_params()
-    bad.pair_sort = 2
+    setattr(bad, field, value)
     ctx = ctypes.c_void_p()
     assert L.sph_create(ctypes.byref(ctx), ctypes.byref(bad), None) == sph.SPH_EINVAL
 
