@@ -109,6 +109,46 @@ def test_neighbour_sets_on_faces_and_edges(oracle_lib):
     assert np.sum(counts == 18) > n ** 3 // 2
 
 
+def test_force_pair_sets_tree_brute_scipy(oracle_lib):
+    """The force enumerates the pairs r_ij < max(h_i, h_j), reached from either
+    side: the k-d tree (which widens each node's reach to its largest h),
+    the O(N^2) scan and scipy's periodic cKDTree (the union of i's sphere
+    and of every j's sphere that holds i) give the same count per particle,
+    on clumps with a 30x spread of h, and the tree and the scan give the
+    same a and du/dt."""
+    rng = np.random.default_rng(19)
+    L = np.array([1.0, 0.8, 1.2])
+    centres = rng.random((4, 3)) * L
+    x = np.concatenate([
+        (centres[rng.integers(0, 4, 1200)] + rng.normal(0.0, 0.04, (1200, 3))) % L,
+        rng.random((600, 3)) * L])
+    n = x.shape[0]
+    h = np.exp(rng.uniform(np.log(0.006), np.log(0.18), n))
+    v = rng.normal(0.0, 0.3, (n, 3))
+    m = np.full(n, 1.0 / n)
+    u = rng.uniform(0.5, 1.5, n)
+    rho = rng.uniform(0.5, 2.0, n)
+    omega = rng.uniform(0.8, 1.2, n)
+    ft = oracle.force(x, v, m, u, h, rho, omega, L, 5.0 / 3.0, use_tree=True)
+    fb = oracle.force(x, v, m, u, h, rho, omega, L, 5.0 / 3.0, use_tree=False)
+    t = cKDTree(x, boxsize=L)
+    reach = [set(t.query_ball_point(x[i], h[i])) - {i} for i in range(n)]
+    for j in range(n):
+        for i in t.query_ball_point(x[j], h[j]):
+            if i != j:
+                reach[i].add(j)
+    want = np.array([len(r) for r in reach])
+    np.testing.assert_array_equal(ft["count"], want)
+    np.testing.assert_array_equal(fb["count"], want)
+    # pairs reached only through j's larger h are a real share of the set
+    own = np.array([len(t.query_ball_point(x[i], h[i])) - 1 for i in range(n)])
+    assert (want - own).sum() > 0.2 * want.sum()
+    amax = np.abs(fb["a"]).max()
+    np.testing.assert_allclose(ft["a"], fb["a"], rtol=0, atol=1e-12 * amax)
+    dmax = np.abs(fb["dudt"]).max()
+    np.testing.assert_allclose(ft["dudt"], fb["dudt"], rtol=0, atol=1e-12 * dmax)
+
+
 # --------------------------------------------------- h root and density
 
 @pytest.fixture(scope="module")
