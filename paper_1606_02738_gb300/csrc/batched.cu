@@ -564,7 +564,7 @@ struct DensSmem {
   unsigned short cand[kNW][kCandD];         // each warp's pre-filtered entries
   unsigned short list[kNW][dens_lane(NS) * 32];  // [entry][lane]
   int wcount[kNW];
-  int qslot[4];                             // work queue: claimed chunks (two slots)
+  int qslot[8];                             // work queue: claimed chunks (two slots), timing
 };
 
 template <int NS>
@@ -576,7 +576,7 @@ struct ForceSmem {
   unsigned short cand[kNW][force_cand(NS)];
   unsigned short list[kNW][force_lane(NS) * 32];
   int wcount[kNW];
-  int qslot[4];                             // work queue: claimed chunks (two slots)
+  int qslot[8];                             // work queue: claimed chunks (two slots), timing
 };
 
 // Group g of a launch: tier 0 walks every group; tier 1 walks the groups
@@ -606,10 +606,9 @@ struct GroupCursor {
   int it;
   int base;        // queue position of the claimed chunk
   unsigned mask;   // its groups still to run
-  int g;           // thread 0: the group being timed, or -1
-  long long t0;
-  template <class Skip>
-  __device__ int fetch(const WorkQueue &wq, int *slot, int ng, Skip skip) {
+  // skip: the launch leaves group g out when sel && (sel[g] != 0) != want
+  __device__ int fetch(const WorkQueue &wq, int head, const unsigned char *sel, bool want,
+                       int *slot, int ng) {
     if (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
@@ -621,11 +620,11 @@ struct GroupCursor {
       unsigned m;
       do {
         b0 = 0;
-        if (threadIdx.x == 0) b0 = atomicAdd(wq.head, kClaim);
+        if (threadIdx.x == 0) b0 = atomicAdd(wq.head + head, kClaim);
         b0 = __shfl_sync(0xffffffffu, b0, 0);
         const int p = b0 + (int)threadIdx.x;
         const int gp = p < ng ? (wq.order ? wq.order[p] : p) : -1;  // -1: past the last group
-        const bool run = gp >= 0 && !skip(gp);
+        const bool run = gp >= 0 && !(sel && (sel[gp] != 0) != want);
         m = __ballot_sync(0xffffffffu, run);
       } while (m == 0u && b0 < ng);
       if (threadIdx.x == 0) {
@@ -641,24 +640,32 @@ struct GroupCursor {
     mask &= mask - 1;
     return base + b;
   }
-  template <class Skip>
-  __device__ int first(const WorkQueue &wq, int *slot, int ng, Skip skip) {
-    g = -1;
+  // slot[4], slot[5]: thread 0's timed group (-1: none) and its start (a
+  // clock64 split in two ints); only thread 0 reads or writes them
+  __device__ int first(const WorkQueue &wq, int head, const unsigned char *sel, bool want,
+                       int *slot, int ng) {
     it = 0;
     mask = 0u;
-    return dyn ? fetch(wq, slot, ng, skip) : (int)blockIdx.x;
+    if (threadIdx.x == 0) slot[4] = -1;
+    return dyn ? fetch(wq, head, sel, want, slot, ng) : (int)blockIdx.x;
   }
-  template <class Skip>
-  __device__ int next(const WorkQueue &wq, int *slot, int ng, int q, Skip skip) {
+  __device__ int next(const WorkQueue &wq, int head, const unsigned char *sel, bool want,
+                      int *slot, int ng, int q) {
     if (!dyn) return q + gridDim.x;
-    if (threadIdx.x == 0 && g >= 0) wq.cost[g] = (float)(clock64() - t0);
-    g = -1;
-    return fetch(wq, slot, ng, skip);
+    if (threadIdx.x == 0 && slot[4] >= 0) {
+      const long long t0 = (long long)(((unsigned long long)(unsigned)slot[6] << 32) |
+                                       (unsigned)slot[5]);
+      wq.cost[slot[4]] = (float)(clock64() - t0);
+      slot[4] = -1;
+    }
+    return fetch(wq, head, sel, want, slot, ng);
   }
-  __device__ void run(int group) {
+  __device__ void run(int *slot, int group) {
     if (dyn && threadIdx.x == 0) {
-      g = group;
-      t0 = clock64();
+      const unsigned long long t0 = (unsigned long long)clock64();
+      slot[4] = group;
+      slot[5] = (int)(unsigned)t0;
+      slot[6] = (int)(unsigned)(t0 >> 32);
     }
   }
 };
@@ -1075,19 +1082,21 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
 
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
   GroupCursor cur;
+  // with the queue: heads [0] and [1] for the launches on stored stages and anew
   cur.dyn = tier == 0 && a.wq.head != nullptr;
-  const WorkQueue wq = {a.wq.order, cur.dyn ? a.wq.head + (REUSE ? 0 : 1) : nullptr, a.wq.cost};
-  const auto skip = [&](int g) { return use_cache && (a.cache.gmode[g] != 0) != REUSE; };
-  const int qn = cur.dyn ? queue_positions(wq, ng) : ng;
-  for (int q = cur.first(wq, S.qslot, qn, skip); q < qn; q = cur.next(wq, S.qslot, qn, q, skip)) {
-    const int g = cur.dyn ? (wq.order ? wq.order[q] : q) : tier_group(tier, q, a.queue);
+  const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
+  for (int q = cur.first(a.wq, REUSE ? 0 : 1, use_cache ? a.cache.gmode : nullptr, REUSE,
+                         S.qslot, qn);
+       q < qn; q = cur.next(a.wq, REUSE ? 0 : 1, use_cache ? a.cache.gmode : nullptr, REUSE,
+                            S.qslot, qn, q)) {
+    const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
     const float hcap = (float)B.hcap;
     const float Rg = fminf(G.hmax * a.skin_stage, wmin);
     if (use_cache && (a.cache.gmode[g] != 0) != REUSE) continue;  // the other instantiation's
-    cur.run(g);
+    cur.run(S.qslot, g);
     // tasks from the tight walk: complete only within each target's own
     // starting radius (block-uniform; a reused stage never came from one)
     const bool tightw = !REUSE && !TIGHT && a.wmode && a.wmode[g];
@@ -1935,13 +1944,12 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
   GroupCursor cur;
   cur.dyn = tier == 0 && a.wq.head != nullptr;
-  const auto skip = [&](int g) { return tier == 0 && a.cache_on && a.cache.fuse[g]; };
   const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
-  for (int q = cur.first(a.wq, S.qslot, qn, skip); q < qn;
-       q = cur.next(a.wq, S.qslot, qn, q, skip)) {
+  for (int q = cur.first(a.wq, 0, a.cache_on ? a.cache.fuse : nullptr, false, S.qslot, qn);
+       q < qn; q = cur.next(a.wq, 0, a.cache_on ? a.cache.fuse : nullptr, false, S.qslot, qn, q)) {
     const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
     if (tier == 0 && a.cache_on && a.cache.fuse[g]) continue;  // done on the cache
-    cur.run(g);
+    cur.run(S.qslot, g);
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
     const int e0 = g * a.tcap;
