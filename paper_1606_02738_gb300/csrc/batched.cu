@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, MODE == kWalkTight ? 4 : 10)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ltmask = (1u << lane) - 1u;
   const int ng = tight ? *a.walk_queued : a.n_groups;
+  // the cached force is skipped in this call: fuse[] is not read (stale)
+  if (far && a.cache.ctl->force_off) return;
   int n_reused = 0, n_failed = 0;
   for (int q = blockIdx.x * kWalkWarps + warp; q < ng; q += gridDim.x * kWalkWarps) {
     const int g = tight ? a.walk_queue[q] : q;
@@ -313,14 +315,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, MODE == kWalkTight ? 4 : 10)
         continue;  // the stored task slots and count stay
       }
     }
-    if (MODE == kWalkPlain && a.cache_on && a.force && a.cache.fuse[g]) {
+    if (MODE == kWalkPlain && a.cache_on && a.force && !a.cache.ctl->force_off &&
+        a.cache.fuse[g]) {
       if (lane == 0) a.count[g] = 0;  // the force reuses the density's cache: no walk
       continue;
     }
     if (far) {
       // candidates: every warp of the group finished its density on lists
       const GroupCache &M = a.cache.meta[g];
-      bool ok = !a.cache.ctl->force_off && M.stage_ok;
+      bool ok = M.stage_ok;
       for (int w = 0; w < 4; ++w)
         if (w * 8 < G.count && !M.wok[w]) ok = false;
       if (!ok) {
@@ -1945,10 +1948,13 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   GroupCursor cur;
   cur.dyn = tier == 0 && a.wq.head != nullptr;
   const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
-  for (int q = cur.first(a.wq, 0, a.cache_on ? a.cache.fuse : nullptr, false, S.qslot, qn);
-       q < qn; q = cur.next(a.wq, 0, a.cache_on ? a.cache.fuse : nullptr, false, S.qslot, qn, q)) {
+  // groups done on the cache (fuse[g], unless the cached force is off in this call)
+  const unsigned char *fuse =
+      tier == 0 && a.cache_on && !a.cache.ctl->force_off ? a.cache.fuse : nullptr;
+  for (int q = cur.first(a.wq, 0, fuse, false, S.qslot, qn); q < qn;
+       q = cur.next(a.wq, 0, fuse, false, S.qslot, qn, q)) {
     const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
-    if (tier == 0 && a.cache_on && a.cache.fuse[g]) continue;  // done on the cache
+    if (fuse && fuse[g]) continue;  // done on the cache
     cur.run(S.qslot, g);
     const Group G = a.groups[g];
     const int nt = a.tcount[g];
@@ -2176,6 +2182,7 @@ static_assert(sizeof(unsigned) * kNW * kSub * ((kStageD + 32) / 32) >= 12 * 384,
 template <bool KAHAN, int NSD>
 __global__ void __launch_bounds__(kNW * 32, force_reuse_min_blocks(NSD))
     k_force_reuse(BatchForceArgs a) {
+  if (a.cache.ctl->force_off) return;  // the cached force is skipped in this call
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceReuseSmem<NSD> &S = *reinterpret_cast<ForceReuseSmem<NSD> *>(smem_raw);
   constexpr int BMW = (NSD + 32) / 32;
