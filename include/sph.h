@@ -79,6 +79,12 @@ extern "C" {
 #define SPH_MODE_PLAIN 0   /* one launch per density pass, host-driven h iteration */
 #define SPH_MODE_BATCHED 1 /* one block per group of <= 32 particles, h iteration inside the
                               kernel; particles it cannot finish go to the per-pass form */
+#define SPH_MODE_SYMMETRIC 2 /* density as SPH_MODE_PLAIN; force from pair tasks between
+                                octree leaves that evaluate each pair once and update both
+                                particles (Section 3.1, pair symmetry), the top cells
+                                coloured so that the cells one launch runs share no
+                                neighbour: no atomics, fixed summation order. FP32 sums
+                                only (precision is not used by this force) */
 
 /* ---- precision ---- */
 #define SPH_PREC_FP32 0  /* FP32 pair arithmetic and accumulation */

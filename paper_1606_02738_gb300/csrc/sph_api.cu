@@ -105,6 +105,10 @@ struct sph_ctx {
   int reuse_streak = 0;            // steps run in a row on the current grid
   int regrids_in_step = 0;
   long long grid_stamp = 0;        // bumped by every regrid (sizes, buffers, store swap)
+  // symmetric force: the coloured cells of the current grid
+  DevBuf sym_cells, sym_cell_leaf, sym_leafcell;
+  std::vector<int> sym_off;
+  long long sym_stamp = -1;
   // steady steps as one CUDA graph (batched form on a reused grid)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -1135,8 +1139,69 @@ int force_batched(sph_ctx *c, VuSel vu_for_force, bool *all_done) {
   return SPH_OK;
 }
 
+// Symmetric force (SPH_MODE_SYMMETRIC): the per-pass force task lists of
+// every leaf, the colour classes of the top cells (once per grid, through
+// the host), then one launch per colour; results accumulate from zero.
+int force_symmetric(sph_ctx *c, VuSel vu_for_force) {
+  GeomArgs ga = geom_args(c);
+  launch_leaf_hmax(ga, c->n_nodes, c->stream);
+  TRY(build_lists(c, true, nullptr, c->n_leaves, c->force_off, c->force_tasks, c->n_force_tasks));
+  const int nl = c->n_leaves;
+  if (c->sym_stamp != c->grid_stamp) {
+    TRY(ensure(c, c->sym_leafcell, sizeof(int) * (size_t)std::max(nl, 1)));
+    launch_leaf_cells(as<Leaf>(c->leaves), as<Node>(c->nodes), nl, as<int>(c->sym_leafcell),
+                      c->stream);
+    std::vector<int> leaf_cell((size_t)nl), cell_leaf, cells;
+    if (nl > 0)
+      CUDA_TRY(cudaMemcpyAsync(leaf_cell.data(), c->sym_leafcell.p, sizeof(int) * (size_t)nl,
+                               cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    sym_colours(c->boxes_h, c->n_cells, leaf_cell, cell_leaf, cells, c->sym_off);
+    TRY(ensure(c, c->sym_cell_leaf, sizeof(int) * cell_leaf.size()));
+    TRY(ensure(c, c->sym_cells, sizeof(int) * std::max(cells.size(), (size_t)1)));
+    CUDA_TRY(cudaMemcpyAsync(c->sym_cell_leaf.p, cell_leaf.data(), sizeof(int) * cell_leaf.size(),
+                             cudaMemcpyHostToDevice, c->stream));
+    if (!cells.empty())
+      CUDA_TRY(cudaMemcpyAsync(c->sym_cells.p, cells.data(), sizeof(int) * cells.size(),
+                               cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    c->sym_stamp = c->grid_stamp;
+  }
+  CUDA_TRY(cudaMemsetAsync(c->st.acc, 0, sizeof(float4) * (size_t)c->n, c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->nforce, 0, sizeof(int) * (size_t)c->n, c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_inter, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&c->ctr->force_cand, 0, sizeof(unsigned long long), c->stream));
+  SymArgs sa{};
+  sa.cell_leaf = as<int>(c->sym_cell_leaf);
+  sa.leaves = as<Leaf>(c->leaves);
+  sa.list_off = as<int>(c->force_off);
+  sa.tasks = as<Task>(c->force_tasks);
+  sa.pm = c->pm;
+  sa.fi = c->fi;
+  sa.vu = vu_of(c, vu_for_force);
+  sa.acc = c->st.acc;
+  sa.nforce = c->nforce;
+  sa.ctr = c->ctr;
+  tic(c, kForce);
+  for (size_t k = 0; k + 1 < c->sym_off.size(); ++k) {
+    sa.cells = as<int>(c->sym_cells) + c->sym_off[k];
+    sa.n_cells = c->sym_off[k + 1] - c->sym_off[k];
+    launch_force_sym(sa, c->stream);
+  }
+  toc(c, kForce);
+  ++c->force_launches;
+  c->force_pending = true;
+  TRY(sync_check(c));
+  c->force_valid = true;
+  return SPH_OK;
+}
+
 int force_impl(sph_ctx *c, VuSel vu_for_force) {
   if (!c->density_valid) return fail(c, SPH_ESTATE, "sph_force needs sph_density first");
+  if (c->p.mode == SPH_MODE_SYMMETRIC) {
+    if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
+    return force_symmetric(c, vu_for_force);
+  }
   if (c->force_pending) TRY(read_counters(c));  // bank the previous force counters
   const int *active = nullptr;
   int n_targets = c->n_leaves;
@@ -1392,7 +1457,7 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
   if (!(q.gamma > 1.0) || !(q.n_ngb > 32.0 / 3.0) || !(q.h_tol > 0.0) || q.max_iter < 1 ||
       q.n_split < 8 || q.n_split > 256 ||
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
-      (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED) ||
+      (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED && q.mode != SPH_MODE_SYMMETRIC) ||
       (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
       (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
       q.reuse_lists < 0 || q.reuse_lists > 2 || q.work_queue < 0 || q.work_queue > 3)
@@ -1718,7 +1783,8 @@ void sph_destroy(sph_ctx *c) {
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
                     &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
                     &c->gqueue,     &c->lflag,      &c->gwmode,   &c->gcost_d,    &c->gcost_f,
-                    &c->gorder,     &c->gbins,      &c->gcbin,      &c->vc_meta,
+                    &c->gorder,     &c->gbins,      &c->gcbin,      &c->sym_cells,
+                    &c->sym_cell_leaf, &c->sym_leafcell, &c->vc_meta,
                     &c->vc_sj,
                     &c->vc_slot,    &c->vc_list,    &c->vc_rl,    &c->vc_dpath,   &c->vc_dmax,
                     &c->vc_gmode,   &c->vc_fuse,    &c->vc_ctl};

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace sph {
 
 // Kernel-launch counter of the context whose API call is running on this
@@ -543,6 +545,28 @@ struct ForceArgs {
   int n;
 };
 void launch_force(const ForceArgs &a, cudaStream_t s);
+
+// ---- symmetric.cu (SPH_MODE_SYMMETRIC force) ----
+struct SymArgs {
+  const int *cells;       // the top cells of one colour class (global ids)
+  int n_cells;
+  const int *cell_leaf;   // [n_cells total + 1] first leaf of each top cell
+  const Leaf *leaves;
+  const int *list_off;    // the per-pass force task lists of every leaf (leaf index order)
+  const Task *tasks;
+  const float4 *pm, *fi, *vu;
+  float4 *acc;            // in/out: a, du/dt (zeroed before the first colour)
+  int *nforce;            // in/out (zeroed before the first colour)
+  DevCounters *ctr;
+};
+void launch_force_sym(const SymArgs &a, cudaStream_t s);
+void launch_leaf_cells(const Leaf *leaves, const Node *nodes, int n_leaves, int *out,
+                       cudaStream_t s);
+// Host: cell_leaf (n_cells + 1), and the cells that hold leaves grouped by
+// colour class (colour_cells, with offsets colour_off).
+void sym_colours(const std::vector<BoxDev> &boxes, int n_cells, const std::vector<int> &leaf_cell,
+                 std::vector<int> &cell_leaf, std::vector<int> &colour_cells,
+                 std::vector<int> &colour_off);
 
 // ---- batched.cu ----
 struct GroupBuildArgs {

@@ -26,7 +26,7 @@ ERROR_NAMES = {SPH_EINVAL: "SPH_EINVAL", SPH_ENOMEM: "SPH_ENOMEM", SPH_ECUDA: "S
 
 SPH_X, SPH_V, SPH_U, SPH_H, SPH_RHO, SPH_OMEGA, SPH_P, SPH_A, SPH_DUDT = range(9)
 SPH_NNGB, SPH_NITER, SPH_NFORCE, SPH_M, SPH_CELL, SPH_LEAF_CELL = 9, 10, 11, 12, 13, 14
-SPH_MODE_PLAIN, SPH_MODE_BATCHED = 0, 1
+SPH_MODE_PLAIN, SPH_MODE_BATCHED, SPH_MODE_SYMMETRIC = 0, 1, 2
 SPH_PREC_FP32, SPH_PREC_KAHAN = 0, 1
 
 # field -> (dtype name, components)
