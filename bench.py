@@ -587,8 +587,9 @@ def run_ours(args, d: Dist):
               ("t_grid_ms", "t_sort_ms", "t_lists_ms", "t_density_ms", "t_ghost_ms",
                "t_force_ms", "t_integrate_ms")}
 
-    # end to end through the C ABI with host buffers: H2D of the inputs from
-    # pinned memory, init + density + force + one KDK step, D2H of x, v, u, h
+    # end to end through the C ABI with host buffers, as a host-driven run
+    # does it: H2D of the particle state from pinned memory, init + density +
+    # force + one KDK step, D2H of x, v, u, h, which are the next step's input
     host = {k: torch.as_tensor(getattr(p, k)).pin_memory() for k in ("x", "v", "m", "u", "h")}
     dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
     outs = {"x": torch.empty((p.n, 3), dtype=torch.float64).pin_memory(),
@@ -615,6 +616,8 @@ def run_ours(args, d: Dist):
         b.record(stream)
         torch.cuda.synchronize(dev)
         sb = ctx.stats()
+        for key in outs:  # the step's result is the next step's input (swap the buffers)
+            host[key], outs[key] = outs[key], host[key]
         if k == 0:
             continue  # first pass warms the allocations
         e2e_ms += a.elapsed_time(b)
@@ -684,8 +687,8 @@ def run_ours(args, d: Dist):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
-                    "step": "H2D inputs, sph_init, sph_density, sph_force, sph_step(dt, 1), "
-                            "D2H x v u h"},
+                    "step": "H2D x v m u h (the previous step's result), sph_init, "
+                            "sph_density, sph_force, sph_step(dt, 1), D2H x v u h"},
             "gpu_launches": int(s1["kernel_launches"] - s0["kernel_launches"]),
             "other_form": other,
             "per_box_launches": per_box,
