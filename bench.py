@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["plain", "batched"], default="batched")
+    ap.add_argument("--mode", choices=["plain", "batched", "symmetric"], default="batched")
     ap.add_argument("--no-pair-sort", action="store_true",
                     help="per-pass form without the pair-axis sorts (whole source leaves)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -351,7 +351,9 @@ def time_form(p, dt, mode, steps, warmup, dev, stream, flush, sph, torch, peak,
     inter_d = s1["total_density_interactions"] - s0["total_density_interactions"]
     inter_f = s1["total_force_interactions"] - s0["total_force_interactions"]
     kern = kernel_roofline(s0, s1, inter_d, inter_f, ms, peak)
-    return {"mode": "plain" if mode == sph.SPH_MODE_PLAIN else "batched", "autotune": tuned,
+    mname = {sph.SPH_MODE_PLAIN: "plain", sph.SPH_MODE_BATCHED: "batched",
+             sph.SPH_MODE_SYMMETRIC: "symmetric"}[mode]
+    return {"mode": mname, "autotune": tuned,
             "dt": dt, "value": (inter_d + inter_f) / (ms / 1000.0), "ms_per_step": ms / steps,
             "interactions_per_step": (inter_d + inter_f) / steps,
             "density_frac": kern["density"]["frac"], "force_frac": kern["force"]["frac"],
@@ -359,21 +361,28 @@ def time_form(p, dt, mode, steps, warmup, dev, stream, flush, sph, torch, peak,
 
 
 def config_summary(headline, args, dev, stream, flush, sph, torch, peak):
-    """The other configurations, both interaction forms, with the bench's
-    protocol (fewer steps): rate, ms per step, batched / per-pass ratio and the
-    FP32 fractions of the interaction kernels."""
+    """The other configurations, both gather forms, with the bench's protocol
+    (fewer steps): rate, ms per step, batched / per-pass ratio and the FP32
+    fractions of the interaction kernels; for sets of at most 1M particles
+    also the symmetric pair-task form (its force serialises each top cell's
+    tasks, so larger sets would take minutes)."""
     out = {}
     for name in ("uniform", "sod", "clustered", "batched", "lognormal"):
         if name == headline:
             continue
         p, dt, wname = workload(name, args.scale)
         rec = {"n_particles": p.n}
-        for mode in (sph.SPH_MODE_BATCHED, sph.SPH_MODE_PLAIN):
+        modes = [sph.SPH_MODE_BATCHED, sph.SPH_MODE_PLAIN]
+        if p.n <= 1_000_000:
+            modes.append(sph.SPH_MODE_SYMMETRIC)
+        for mode in modes:
             r = time_form(p, dt, mode, args.config_steps, 3, dev, stream, flush, sph, torch,
                           peak)
             rec[r["mode"]] = {k: r[k] for k in ("value", "ms_per_step", "density_frac",
                                                 "force_frac", "autotune", "steps")}
         rec["batched_over_plain"] = rec["batched"]["value"] / rec["plain"]["value"]
+        if "symmetric" in rec:
+            rec["batched_over_symmetric"] = rec["batched"]["value"] / rec["symmetric"]["value"]
         out[wname] = rec
         del p
     return out
@@ -507,7 +516,8 @@ def run_ours(args, d: Dist):
     torch.cuda.set_device(d.local)
     dev = torch.device("cuda", d.local)
     p, dt, wname = workload(args.workload, args.scale)
-    mode = sph.SPH_MODE_BATCHED if args.mode == "batched" else sph.SPH_MODE_PLAIN
+    mode = {"batched": sph.SPH_MODE_BATCHED, "plain": sph.SPH_MODE_PLAIN,
+            "symmetric": sph.SPH_MODE_SYMMETRIC}[args.mode]
     stream = torch.cuda.current_stream(dev)
     fixed = {}
     if args.tune:
