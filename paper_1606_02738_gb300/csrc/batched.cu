@@ -582,14 +582,18 @@ struct ForceSmem {
   int qslot[8];                             // work queue: claimed chunks (two slots), timing
 };
 
-// Group g of a launch: tier 0 walks every group; tier 1 walks the groups
-// tier 0 queued because their stage outgrew it (count read on the device,
-// so the second launch needs no host round trip).
-__device__ __forceinline__ int tier_group(int tier, int q, const int *queue) {
-  return tier == 0 ? q : queue[q];
+// Group g of a launch: tier 0 walks every group; tier 1 the groups tier 0
+// queued because their stage outgrew it (restaged by each target's own
+// radius at the first tier's stage size); tier 2 those whose tight stage
+// still outgrew it (the large stage). Counts are read on the device, so the
+// launches need no host round trip.
+__device__ __forceinline__ int tier_group(int tier, int q, const int *queue,
+                                          const int *queue_big) {
+  return tier == 0 ? q : (tier == 1 ? queue[q] : queue_big[q]);
 }
-__device__ __forceinline__ int tier_count(int tier, int n_groups, const int *queued) {
-  return tier == 0 ? n_groups : *queued;
+__device__ __forceinline__ int tier_count(int tier, int n_groups, const int *queued,
+                                          const int *queued_big) {
+  return tier == 0 ? n_groups : (tier == 1 ? *queued : *queued_big);
 }
 
 // The block-uniform cursor of a first-tier group loop. With a work queue,
@@ -1064,12 +1068,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-template <bool KAHAN, int NS, bool REUSE>
+template <bool KAHAN, int NS, bool REUSE, bool MID>
 __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     k_density_batched(BatchDensArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DensSmem<NS> &S = *reinterpret_cast<DensSmem<NS> *>(smem_raw);
-  constexpr bool TIGHT = NS == kBigStageD;  // the second tier stages by each target's radius
+  // the second and later tiers stage by each target's own radius
+  constexpr bool TIGHT = MID || NS == kBigStageD;
   constexpr int LANE = dens_lane(NS);
   const double tol_n = a.tol * a.n_ngb;
   const float gm1 = (float)(a.gamma - 1.0);
@@ -1083,7 +1088,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
   // the neighbour cache: first tier only
   const bool use_cache = !TIGHT && a.cache_on;
 
-  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0]);
+  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[0], &a.ctr->queued_big[0]);
   GroupCursor cur;
   // with the queue: heads [0] and [1] for the launches on stored stages and anew
   cur.dyn = tier == 0 && a.wq.head != nullptr;
@@ -1092,7 +1097,8 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
                          S.qslot, qn);
        q < qn; q = cur.next(a.wq, REUSE ? 0 : 1, use_cache ? a.cache.gmode : nullptr, REUSE,
                             S.qslot, qn, q)) {
-    const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
+    const int g =
+        cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue, a.queue_big);
     const Group G = a.groups[g];
     const BoxDev &B = a.boxes[G.box];
     const float wmin = fminf(B.wf[0], fminf(B.wf[1], B.wf[2]));
@@ -1149,10 +1155,13 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
       if (use_cache && threadIdx.x < kNW) M->wok[threadIdx.x] = 0;
-      if (threadIdx.x < kNW && (TIGHT || nt > a.tcap))  // the third tier walks its targets
+      if (MID && nt <= a.tcap) {  // the tight stage outgrew this size: the large one
+        if (threadIdx.x == 0) a.queue_big[atomicAdd(&a.ctr->queued_big[0], 1)] = g;
+      } else if (threadIdx.x < kNW && (TIGHT || nt > a.tcap)) {  // the third tier walks them
         a.queue2[atomicAdd(&a.ctr->queued2[0], 1)] = g * kNW + threadIdx.x;
-      else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap)  // second tier: tight stage
+      } else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap) {  // second tier: tight stage
         a.queue[atomicAdd(&a.ctr->queued[0], 1)] = g;
+      }
       continue;
     }
     // this warp's targets: lane = target * kSlice + slice
@@ -1830,19 +1839,19 @@ int resident_blocks(K kernel, int bytes) {
   return std::max(per, 1) * std::max(sms, 1);
 }
 
-template <bool KAHAN, int NS, bool REUSE = false>
+template <bool KAHAN, int NS, bool REUSE = false, bool MID = false>
 void launch_density_tier(const BatchDensArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
   static int resident = 0;
   const int bytes = (int)sizeof(DensSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_density_batched<KAHAN, NS, REUSE>,
+    cudaFuncSetAttribute(k_density_batched<KAHAN, NS, REUSE, MID>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    resident = resident_blocks(k_density_batched<KAHAN, NS, REUSE>, bytes);
+    resident = resident_blocks(k_density_batched<KAHAN, NS, REUSE, MID>, bytes);
     attr = true;
   }
   if (tier == 0 && a.wq.head) blocks = std::min(a.n_groups, resident);
-  k_density_batched<KAHAN, NS, REUSE><<<blocks, kNW * 32, bytes, s>>>(a, tier);
+  k_density_batched<KAHAN, NS, REUSE, MID><<<blocks, kNW * 32, bytes, s>>>(a, tier);
   note_launch();
 }
 
@@ -1898,38 +1907,43 @@ void launch_cache_decide(CacheCtl *ctl, cudaStream_t s) {
 int cache_stage_slots(int tile) { return tile ? kStageDL : kStageD; }
 int cache_lane_cap(int tile) { return dens_lane(tile ? kStageDL : kStageD); }
 
-// Tier 0 over every group, then tier 1 (4x the stage, 2 blocks per SM) over
-// the groups tier 0 queued; `a.ctr->queued` and `a.queue` must be zeroed /
-// sized for n_groups by the caller.
+// Tier 0 over every group; tier 1 over the groups tier 0 queued, restaged by
+// each target's own radius at the first tier's stage size (same occupancy);
+// tier 2 (large stage, 2 blocks per SM) over those whose tight stage still
+// outgrew it; then the third tier. `a.ctr` queue counts must be zeroed and
+// the queues sized for n_groups by the caller.
+template <bool KAHAN>
+void launch_density_tiers(const BatchDensArgs &a, int blocks, int big, cudaStream_t s) {
+  if (a.tile) {
+    launch_density_first<KAHAN, kStageDL>(a, blocks, s);
+    launch_density_tier<KAHAN, kStageDL, false, true>(a, 1, blocks, s);
+  } else {
+    launch_density_first<KAHAN, kStageD>(a, blocks, s);
+    launch_density_tier<KAHAN, kStageD, false, true>(a, 1, blocks, s);
+  }
+  launch_density_tier<KAHAN, kBigStageD>(a, 2, big, s);
+  k_density_stream<KAHAN><<<152 * 8, 128, 0, s>>>(a);
+  note_launch();
+}
+
 void launch_density_batched(const BatchDensArgs &a, cudaStream_t s) {
   if (a.n_groups <= 0) return;
   const int blocks = a.n_groups < 152 * 64 ? a.n_groups : 152 * 64;
   const int big = a.n_groups < 152 * 2 ? a.n_groups : 152 * 2;
-  if (a.kahan) {
-    if (a.tile)
-      launch_density_first<true, kStageDL>(a, blocks, s);
-    else
-      launch_density_first<true, kStageD>(a, blocks, s);
-    launch_density_tier<true, kBigStageD>(a, 1, big, s);
-    k_density_stream<true><<<152 * 8, 128, 0, s>>>(a);
-  } else {
-    if (a.tile)
-      launch_density_first<false, kStageDL>(a, blocks, s);
-    else
-      launch_density_first<false, kStageD>(a, blocks, s);
-    launch_density_tier<false, kBigStageD>(a, 1, big, s);
-    k_density_stream<false><<<152 * 8, 128, 0, s>>>(a);
-  }
-  note_launch();
+  if (a.kahan)
+    launch_density_tiers<true>(a, blocks, big, s);
+  else
+    launch_density_tiers<false>(a, blocks, big, s);
 }
 
 
-template <bool KAHAN, int NS>
+template <bool KAHAN, int NS, bool MID>
 __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     k_force_batched(BatchForceArgs a, int tier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ForceSmem<NS> &S = *reinterpret_cast<ForceSmem<NS> *>(smem_raw);
-  constexpr bool TIGHT = NS == kBigStageF;  // the second tier stages by each target's radius
+  // the second and later tiers stage by each target's own radius
+  constexpr bool TIGHT = MID || NS == kBigStageF;
   constexpr int CANDF = force_cand(NS);
   constexpr int LANE = force_lane(NS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1944,7 +1958,7 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
     S.sj[NS] = 0;
   }
 
-  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1]);
+  const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1], &a.ctr->queued_big[1]);
   GroupCursor cur;
   cur.dyn = tier == 0 && a.wq.head != nullptr;
   const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
@@ -1953,7 +1967,8 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
       tier == 0 && a.cache_on && !a.cache.ctl->force_off ? a.cache.fuse : nullptr;
   for (int q = cur.first(a.wq, 0, fuse, false, S.qslot, qn); q < qn;
        q = cur.next(a.wq, 0, fuse, false, S.qslot, qn, q)) {
-    const int g = cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue);
+    const int g =
+        cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue, a.queue_big);
     if (fuse && fuse[g]) continue;  // done on the cache
     cur.run(S.qslot, g);
     const Group G = a.groups[g];
@@ -1975,10 +1990,13 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
                           TIGHT ? S.tgt : nullptr);
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
-      if (threadIdx.x < kNW && (TIGHT || nt > a.tcap))  // the third tier walks its targets
+      if (MID && nt <= a.tcap) {  // the tight stage outgrew this size: the large one
+        if (threadIdx.x == 0) a.queue_big[atomicAdd(&a.ctr->queued_big[1], 1)] = g;
+      } else if (threadIdx.x < kNW && (TIGHT || nt > a.tcap)) {  // the third tier walks them
         a.queue2[atomicAdd(&a.ctr->queued2[1], 1)] = g * kNW + threadIdx.x;
-      else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap)  // second tier: tight stage
+      } else if (threadIdx.x == 0 && !TIGHT && nt <= a.tcap) {  // second tier: tight stage
         a.queue[atomicAdd(&a.ctr->queued[1], 1)] = g;
+      }
       continue;
     }
     const int tloc = warp * kSub + (lane >> 2);
@@ -2299,19 +2317,35 @@ void launch_force_reuse(const BatchForceArgs &a, int blocks, cudaStream_t s) {
   note_launch();
 }
 
-template <bool KAHAN, int NS>
+template <bool KAHAN, int NS, bool MID = false>
 void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream_t s) {
   static bool attr = false;
   static int resident = 0;
   const int bytes = (int)sizeof(ForceSmem<NS>);
   if (!attr) {
-    cudaFuncSetAttribute(k_force_batched<KAHAN, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
-    resident = resident_blocks(k_force_batched<KAHAN, NS>, bytes);
+    cudaFuncSetAttribute(k_force_batched<KAHAN, NS, MID>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    resident = resident_blocks(k_force_batched<KAHAN, NS, MID>, bytes);
     attr = true;
   }
   if (tier == 0 && a.wq.head) blocks = std::min(a.n_groups, resident);
-  k_force_batched<KAHAN, NS><<<blocks, kNW * 32, bytes, s>>>(a, tier);
+  k_force_batched<KAHAN, NS, MID><<<blocks, kNW * 32, bytes, s>>>(a, tier);
+  note_launch();
+}
+
+// The force's tiers, as the density's: first tier, the tight tier at the
+// first tier's stage size, the large-stage tier, the third tier.
+template <bool KAHAN>
+void launch_force_tiers(const BatchForceArgs &a, int blocks, int big, cudaStream_t s) {
+  if (a.tile) {
+    launch_force_tier<KAHAN, kStageFL>(a, 0, blocks, s);
+    launch_force_tier<KAHAN, kStageFL, true>(a, 1, blocks, s);
+  } else {
+    launch_force_tier<KAHAN, kStageF>(a, 0, blocks, s);
+    launch_force_tier<KAHAN, kStageF, true>(a, 1, blocks, s);
+  }
+  launch_force_tier<KAHAN, kBigStageF>(a, 2, big, s);
+  k_force_stream<KAHAN><<<152 * 8, 128, 0, s>>>(a);
   note_launch();
 }
 
@@ -2332,22 +2366,10 @@ void launch_force_batched(const BatchForceArgs &a, cudaStream_t s) {
         launch_force_reuse<false, kStageD>(a, blocks, s);
     }
   }
-  if (a.kahan) {
-    if (a.tile)
-      launch_force_tier<true, kStageFL>(a, 0, blocks, s);
-    else
-      launch_force_tier<true, kStageF>(a, 0, blocks, s);
-    launch_force_tier<true, kBigStageF>(a, 1, big, s);
-    k_force_stream<true><<<152 * 8, 128, 0, s>>>(a);
-  } else {
-    if (a.tile)
-      launch_force_tier<false, kStageFL>(a, 0, blocks, s);
-    else
-      launch_force_tier<false, kStageF>(a, 0, blocks, s);
-    launch_force_tier<false, kBigStageF>(a, 1, big, s);
-    k_force_stream<false><<<152 * 8, 128, 0, s>>>(a);
-  }
-  note_launch();
+  if (a.kahan)
+    launch_force_tiers<true>(a, blocks, big, s);
+  else
+    launch_force_tiers<false>(a, blocks, big, s);
 }
 
 }  // namespace sph

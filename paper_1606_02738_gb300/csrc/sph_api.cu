@@ -701,7 +701,8 @@ int build_groups(sph_ctx *c) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->n_groups = ng;
   TRY(ensure(c, c->groups, sizeof(Group) * (size_t)std::max(ng, 1)));
-  TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1) * 5));  // queue, queue2
+  // queue, queue2 (4 per group), queue_big
+  TRY(ensure(c, c->gqueue, sizeof(int) * (size_t)std::max(ng, 1) * 6));
   // new groups: no measured cost yet (the first order is the estimate)
   TRY(ensure(c, c->gcost_d, sizeof(float) * (size_t)std::max(ng, 1)));
   TRY(ensure(c, c->gcost_f, sizeof(float) * (size_t)std::max(ng, 1)));
@@ -929,6 +930,7 @@ int enqueue_density_batched(sph_ctx *c, VuSel vu_for_P, bool hmax_current = fals
   da.ctr = c->ctr;
   da.queue = as<int>(c->gqueue);  // ctr->queued, queued2 were zeroed with the counters
   da.queue2 = as<int>(c->gqueue) + c->n_groups;
+  da.queue_big = as<int>(c->gqueue) + 5 * (size_t)c->n_groups;
   da.gpos = c->gpos;
   da.tile = c->p.tile;
   da.nodes = as<Node>(c->nodes);
@@ -1093,6 +1095,7 @@ int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
     CUDA_TRY(cudaMemsetAsync(&c->ctr->unconverged, 0, sizeof(int), c->stream));
     CUDA_TRY(cudaMemsetAsync(&c->ctr->queued[1], 0, sizeof(int), c->stream));
     CUDA_TRY(cudaMemsetAsync(&c->ctr->queued2[1], 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaMemsetAsync(&c->ctr->queued_big[1], 0, sizeof(int), c->stream));
     CUDA_TRY(cudaMemsetAsync(c->fdone, 0, (size_t)c->n, c->stream));
   }
   BatchForceArgs fa{};
@@ -1112,6 +1115,7 @@ int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
   fa.ctr = c->ctr;
   fa.queue = as<int>(c->gqueue);
   fa.queue2 = as<int>(c->gqueue) + c->n_groups;
+  fa.queue_big = as<int>(c->gqueue) + 5 * (size_t)c->n_groups;
   fa.gpos = c->gpos;
   fa.tile = c->p.tile;
   fa.nodes = as<Node>(c->nodes);

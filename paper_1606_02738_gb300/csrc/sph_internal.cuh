@@ -104,6 +104,8 @@ struct DevCounters {
                                       // neighbour cache (no walk, no staging tests)
   int cache_built;                    // groups whose density built (and stored) a new cache
   int cache_relist;                   // warps on a stored stage that rebuilt their lists
+  int queued_big[2];                  // groups the tight tier at the first-tier stage size
+                                      // passed on to the large-stage tier
   int step_status;                    // kErr* bits of the kicks and the grid check (last
                                       // field: the density's counter reset keeps it)
 };
@@ -723,8 +725,9 @@ struct BatchDensArgs {
   float *rho, *omega, *P;
   float4 *fi;
   DevCounters *ctr;
-  int *queue;            // [n_groups] groups handed to the second tier
+  int *queue;            // [n_groups] groups handed to the second tier (tight stage)
   int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
+  int *queue_big;        // [n_groups] groups the second tier hands to its large stage
   const Node *nodes;     // the third tier walks the octrees itself
   int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
   // per group, 1: its tasks came from the tight walk, so its stage is complete
@@ -769,8 +772,9 @@ struct BatchForceArgs {
   int *nforce;
   unsigned char *fdone;  // per particle: force written by the batched kernel
   DevCounters *ctr;
-  int *queue;            // [n_groups] groups handed to the second tier
+  int *queue;            // [n_groups] groups handed to the second tier (tight stage)
   int *queue2;           // [n_groups * 4] (group, warp) handed to the third tier
+  int *queue_big;        // [n_groups] groups the second tier hands to its large stage
   const Node *nodes;     // the third tier walks the octrees itself
   const BoxDev *boxes;
   int kahan;             // compensated sums
