@@ -487,13 +487,25 @@ __global__ void k_leaf_geometry(GeomArgs a) {
   }
   for (int o = 16; o; o >>= 1) out = fmaxf(out, __shfl_xor_sync(0xffffffffu, out, o));
   if (lane == 0) {
+    // up the tree until a node's box already holds this leaf's: the leaf that
+    // gave it those bounds takes them further up itself (a node's lo only
+    // falls and hi only rises within the launch, so a stale read can only
+    // cost an extra atomic, never skip a needed one)
     int id = L.node;
     while (id >= 0) {
       Node *n = &a.nodes[id];
+      bool held = true;
       for (int d = 0; d < 3; ++d) {
-        atomic_min_f(&n->lo[d], lo[d]);
-        atomic_max_f(&n->hi[d], hi[d]);
+        if (lo[d] < n->lo[d]) {
+          atomic_min_f(&n->lo[d], lo[d]);
+          held = false;
+        }
+        if (hi[d] > n->hi[d]) {
+          atomic_max_f(&n->hi[d], hi[d]);
+          held = false;
+        }
       }
+      if (held) break;
       id = n->parent;
     }
     if (a.maxout && out > 0.f) atomicMax(&a.maxout[L.box], __float_as_uint(out));
@@ -533,9 +545,9 @@ __global__ void k_leaf_hmax(GeomArgs a) {
   float hm = 0.f;
   for (int k = lane; k < L.count; k += 32) hm = fmaxf(hm, a.hf[L.start + k]);
   for (int o = 16; o; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-  if (lane == 0) {
+  if (lane == 0) {  // up the tree until a node already holds hm (as in k_leaf_geometry)
     int id = L.node;
-    while (id >= 0) {
+    while (id >= 0 && hm > a.nodes[id].hmax) {
       atomic_max_pos(&a.nodes[id].hmax, hm);
       id = a.nodes[id].parent;
     }
