@@ -189,9 +189,10 @@ typedef struct {
   int32_t fallback_causes[4];
   /* Batched form, last sph_density + sph_force ([0] density, [1] force):
    * groups whose stage overflowed and that the second tier staged again by
-   * each target's own radius, and (group, warp) entries whose targets the
-   * third tier computed one warp per target (stage or task-slot overflow, or
-   * an h beyond the staged radius). */
+   * each target's own radius (first at the first tier's stage size, then,
+   * if that still overflowed, in a larger stage), and (group, warp) entries
+   * whose targets the third tier computed one warp per target (stage or
+   * task-slot overflow, or an h beyond the staged radius). */
   int32_t tier2_groups[2];
   int32_t tier3_entries[2];
   int64_t sort_launches;      /* pair-axis sort launches (cumulative since sph_create) */
