@@ -114,7 +114,10 @@ typedef struct {
                       only, and runs those steps as one CUDA graph in the batched FP32
                       form; 0: regrid every step (same results up to summation order) */
   int tile;        /* batched first-tier stage: 0 small (more blocks per SM), 1 large
-                      (fewer groups to the second tier on clumped inputs) */
+                      (fewer groups to the second tier on clumped inputs), 2 the density
+                      as 1 and the force's first tier per group: the small stage for the
+                      groups whose stage in the last force call held <= 640 entries, the
+                      large one for the rest (an occupancy bin per group) */
   double cell_factor; /* top-cell edge >= cell_factor x the largest h where the box allows
                          (1 <= cell_factor <= 4; >= 1 x always) */
   int reuse_lists;  /* batched form, neighbour cache: keep each group's staged neighbours

@@ -1828,6 +1828,34 @@ void launch_cost_order(const Group *groups, int n_groups, const int *tcount, con
   note_launch();
 }
 
+// ------------------------------------------------------ tile 2 partition
+
+__global__ void k_bin_flag(const int *gstage, int n, int fit, int *flag) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) flag[g] = gstage[g] >= 0 && gstage[g] <= fit ? 1 : 0;
+  if (g == n) flag[g] = 0;
+}
+
+__global__ void k_bin_scatter(int n, const int *flag, const int *excl, int *order, int *split) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int ns = excl[n];
+  order[flag[g] ? excl[g] : ns + g - excl[g]] = g;
+  if (g == 0) *split = ns;
+}
+
+void launch_force_bins(const int *gstage, int n_groups, int fit, int *flag, int *excl,
+                       void *scan_tmp, size_t scan_tmp_bytes, int *order, int *split,
+                       cudaStream_t s) {
+  if (n_groups <= 0) return;
+  const int nb = (n_groups + 1 + 255) / 256;
+  k_bin_flag<<<nb, 256, 0, s>>>(gstage, n_groups, fit, flag);
+  note_launch();
+  exclusive_scan_int(flag, excl, n_groups + 1, scan_tmp, scan_tmp_bytes, s);
+  k_bin_scatter<<<nb, 256, 0, s>>>(n_groups, flag, excl, order, split);
+  note_launch();
+}
+
 // Blocks of `kernel` resident on the whole GPU at once (the grid of a
 // launch that claims its groups from a work queue).
 template <class K>
@@ -1961,14 +1989,24 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
   const int ng = tier_count(tier, a.n_groups, &a.ctr->queued[1], &a.ctr->queued_big[1]);
   GroupCursor cur;
   cur.dyn = tier == 0 && a.wq.head != nullptr;
-  const int qn = cur.dyn ? queue_positions(a.wq, ng) : ng;
+  // tile 2: this launch's part of the partitioned groups (with its own queue head)
+  const bool binned = tier == 0 && a.bin > 0;
+  const int blo = binned ? (a.bin == 2 ? *a.bsplit : 0) : 0;
+  const int bhi = binned ? (a.bin == 2 ? a.n_groups : *a.bsplit) : 0;
+  WorkQueue wq = a.wq;
+  if (binned) {
+    wq.order = a.border + blo;
+    if (wq.head) wq.head += a.bin - 1;
+  }
+  const int qn = binned ? bhi - blo : (cur.dyn ? queue_positions(a.wq, ng) : ng);
   // groups done on the cache (fuse[g], unless the cached force is off in this call)
   const unsigned char *fuse =
       tier == 0 && a.cache_on && !a.cache.ctl->force_off ? a.cache.fuse : nullptr;
-  for (int q = cur.first(a.wq, 0, fuse, false, S.qslot, qn); q < qn;
-       q = cur.next(a.wq, 0, fuse, false, S.qslot, qn, q)) {
-    const int g =
-        cur.dyn ? (a.wq.order ? a.wq.order[q] : q) : tier_group(tier, q, a.queue, a.queue_big);
+  for (int q = cur.first(wq, 0, fuse, false, S.qslot, qn); q < qn;
+       q = cur.next(wq, 0, fuse, false, S.qslot, qn, q)) {
+    const int g = binned ? a.border[blo + q]
+                         : (cur.dyn ? (wq.order ? wq.order[q] : q)
+                                    : tier_group(tier, q, a.queue, a.queue_big));
     if (fuse && fuse[g]) continue;  // done on the cache
     cur.run(S.qslot, g);
     const Group G = a.groups[g];
@@ -1988,6 +2026,9 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
         stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane, G.hmax, S.sq,
                           S.sf, S.sj, S.wcount, (unsigned char *)cand, NS,
                           TIGHT ? S.tgt : nullptr);
+    // for tile 2: the stage this group needs (its warps' segments are equal, so
+    // the largest share decides whether it fits)
+    if (tier == 0 && a.gstage && threadIdx.x == 0) a.gstage[g] = sr.maxw * kNW;
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
       if (MID && nt <= a.tcap) {  // the tight stage outgrew this size: the large one
@@ -2337,7 +2378,14 @@ void launch_force_tier(const BatchForceArgs &a, int tier, int blocks, cudaStream
 // first tier's stage size, the large-stage tier, the third tier.
 template <bool KAHAN>
 void launch_force_tiers(const BatchForceArgs &a, int blocks, int big, cudaStream_t s) {
-  if (a.tile) {
+  if (a.tile == 2) {  // per group: the small stage where the last one fitted, else the large
+    BatchForceArgs a0 = a, a1 = a;
+    a0.bin = 1;
+    a1.bin = 2;
+    launch_force_tier<KAHAN, kStageF>(a0, 0, blocks, s);
+    launch_force_tier<KAHAN, kStageFL>(a1, 0, blocks, s);
+    launch_force_tier<KAHAN, kStageFL, true>(a, 1, blocks, s);
+  } else if (a.tile) {
     launch_force_tier<KAHAN, kStageFL>(a, 0, blocks, s);
     launch_force_tier<KAHAN, kStageFL, true>(a, 1, blocks, s);
   } else {

@@ -81,6 +81,8 @@ struct sph_ctx {
   // task cost ordering: measured cost per group (density, force), the order
   // of the next first-tier launch, its bins and queue heads
   DevBuf gcost_d, gcost_f, gorder, gbins, gcbin;
+  // tile 2: each group's last first-tier force stage size, and the partition
+  DevBuf gstage, gbflag, gbexcl, gborder, gbsplit;
   int n_groups = 0;
   bool groups_valid = false;
   int64_t n_gd_tasks = 0, n_gf_tasks = 0;
@@ -710,6 +712,13 @@ int build_groups(sph_ctx *c) {
   TRY(ensure(c, c->gorder, sizeof(int) * n_chunks * 32));
   TRY(ensure(c, c->gbins, sizeof(int) * (kCostBins + 4)));
   TRY(ensure(c, c->gcbin, sizeof(int) * n_chunks));
+  TRY(ensure(c, c->gstage, sizeof(int) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, c->gbflag, sizeof(int) * (size_t)(ng + 1)));
+  TRY(ensure(c, c->gbexcl, sizeof(int) * (size_t)(ng + 1)));
+  TRY(ensure(c, c->gborder, sizeof(int) * (size_t)std::max(ng, 1)));
+  TRY(ensure(c, c->gbsplit, sizeof(int)));
+  // new groups: no stage measured yet (tile 2 puts them on the large stage)
+  CUDA_TRY(cudaMemsetAsync(c->gstage.p, 0xff, sizeof(int) * (size_t)std::max(ng, 1), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->gcost_d.p, 0, sizeof(float) * (size_t)std::max(ng, 1), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->gcost_f.p, 0, sizeof(float) * (size_t)std::max(ng, 1), c->stream));
   ga = group_args(c);
@@ -862,6 +871,10 @@ const float4 *vu_of(const sph_ctx *c, VuSel sel) {
 // GPU holds at once. Below that a claim is a large share of a block's work
 // and the fixed grid stride balances as well.
 constexpr int kQueueMinGroups = 1 << 20;
+
+// Tile 2: a group takes the small first-tier force stage (704 entries) when
+// its last stage held at most this many (a margin for the motion since).
+constexpr int kForceSmallFit = 640;
 
 // 0: grid stride; 1: work queue in group order; 2: work queue in measured
 // cost order.
@@ -1123,7 +1136,16 @@ int enqueue_force_batched(sph_ctx *c, VuSel vu_for_force, bool steady = false) {
   fa.kahan = c->p.precision == SPH_PREC_KAHAN;
   fa.cache_on = cache_on(c) && c->vc_valid;
   if (fa.cache_on) fa.cache = cache_args(c);
-  if (queue_mode(c)) work_queue(c, as<int>(c->gf_off), as<float>(c->gcost_f), 2, 1, fa.wq);
+  fa.gstage = as<int>(c->gstage);
+  if (c->p.tile == 2) {  // the small stage for the groups whose last stage fitted it
+    launch_force_bins(as<int>(c->gstage), c->n_groups, kForceSmallFit, as<int>(c->gbflag),
+                      as<int>(c->gbexcl), c->scan_tmp.p, c->scan_tmp.bytes,
+                      as<int>(c->gborder), as<int>(c->gbsplit), c->stream);
+    fa.border = as<int>(c->gborder);
+    fa.bsplit = as<int>(c->gbsplit);
+  }
+  // heads [2], [3]: the force's first-tier launch(es)
+  if (queue_mode(c)) work_queue(c, as<int>(c->gf_off), as<float>(c->gcost_f), 2, 2, fa.wq);
   tic(c, kForce);
   launch_force_batched(fa, c->stream);
   toc(c, kForce);
@@ -1463,7 +1485,7 @@ int sph_create(sph_ctx **out, const sph_params *p, void *cuda_stream) {
       (q.precision != SPH_PREC_FP32 && q.precision != SPH_PREC_KAHAN) ||
       (q.mode != SPH_MODE_PLAIN && q.mode != SPH_MODE_BATCHED && q.mode != SPH_MODE_SYMMETRIC) ||
       (q.pair_sort != 0 && q.pair_sort != 1) || (q.reuse_grid != 0 && q.reuse_grid != 1) ||
-      (q.tile != 0 && q.tile != 1) || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
+      q.tile < 0 || q.tile > 2 || !(q.cell_factor >= 1.0 && q.cell_factor <= 4.0) ||
       q.reuse_lists < 0 || q.reuse_lists > 2 || q.work_queue < 0 || q.work_queue > 3)
     return SPH_EINVAL;
   sph_ctx *c = new (std::nothrow) sph_ctx();
@@ -1658,7 +1680,7 @@ int sph_autotune(sph_ctx *c, int *tile_out, int *n_split_out, double *cell_facto
     cudaEventDestroy(e0);
     return fail(c, SPH_ECUDA, "event creation failed");
   }
-  const int tiles = c->p.mode == SPH_MODE_BATCHED ? 2 : 1;
+  const int tiles = c->p.mode == SPH_MODE_BATCHED ? 3 : 1;
   const int splits[] = {16, 32, 64, 128};
   const double factors[] = {1.5, 2.0, 2.5, 3.0};
   double best = 1e300;
@@ -1787,7 +1809,8 @@ void sph_destroy(sph_ctx *c) {
                     &c->dens_tasks, &c->force_off,  &c->force_tasks, &c->gcount,
                     &c->groups,     &c->gd_off,     &c->gd_tasks, &c->gf_off,     &c->gf_tasks,
                     &c->gqueue,     &c->lflag,      &c->gwmode,   &c->gcost_d,    &c->gcost_f,
-                    &c->gorder,     &c->gbins,      &c->gcbin,      &c->sym_cells,
+                    &c->gorder,     &c->gbins,      &c->gcbin,      &c->gstage,
+                    &c->gbflag,     &c->gbexcl,     &c->gborder,    &c->gbsplit,    &c->sym_cells,
                     &c->sym_cell_leaf, &c->sym_leafcell, &c->vc_meta,
                     &c->vc_sj,
                     &c->vc_slot,    &c->vc_list,    &c->vc_rl,    &c->vc_dpath,   &c->vc_dmax,

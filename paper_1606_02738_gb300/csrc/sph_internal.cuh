@@ -778,12 +778,24 @@ struct BatchForceArgs {
   const Node *nodes;     // the third tier walks the octrees itself
   const BoxDev *boxes;
   int kahan;             // compensated sums
-  int tile;              // first-tier stage size: 0 small (high occupancy), 1 large
+  int tile;              // first-tier stage size: 0 small (high occupancy), 1 large,
+                         // 2 per group by its last stage (gstage): small where it fitted
   int cache_on;
   CacheArgs cache;
   WorkQueue wq;          // first tier: the work queue
+  int *gstage;           // [n_groups] out, first tier: the stage each group needed, kNW x its
+                         // largest warp share (-1 unknown)
+  const int *border;     // tile 2: the groups, those for the small stage first
+  const int *bsplit;     // tile 2: how many are for the small stage (device)
+  int bin;               // first-tier launch of tile 2: 1 small, 2 large; 0 otherwise
 };
 void launch_force_batched(const BatchForceArgs &a, cudaStream_t s);
+// Tile 2: the groups whose last first-tier force stage held at most `fit`
+// entries (and was measured) first, the rest after, each part in group
+// order; *split = the size of the first part. flag, excl: n_groups + 1 ints.
+void launch_force_bins(const int *gstage, int n_groups, int fit, int *flag, int *excl,
+                       void *scan_tmp, size_t scan_tmp_bytes, int *order, int *split,
+                       cudaStream_t s);
 
 // ---- integrate.cu ----
 struct StoreArrays {

@@ -45,11 +45,14 @@ def test_clustered_from_flat_guess_uses_tiers_2_and_3(precision, tile):
     force_counts_close(g, s)
 
 
-def test_clustered_steady_state_second_call():
+@pytest.mark.parametrize("tile", [0, 2])
+def test_clustered_steady_state_second_call(tile):
     """At converged h (second density + force on the same state) the tiers
-    still give the oracle's values."""
+    still give the oracle's values; with tile 2 the second force call runs
+    the first tier in two parts, the small stage for the groups whose first
+    call's stage fitted it and the large one for the rest."""
     p = inputs.clustered(60000, n_spheres=8, seed=12, sigma_v=0.1)
-    c = sph.Context(mode=sph.SPH_MODE_BATCHED).load(p)
+    c = sph.Context(mode=sph.SPH_MODE_BATCHED, tile=tile).load(p)
     c.density()
     c.force()
     c.density()
