@@ -271,7 +271,7 @@ int sph_get(sph_ctx *ctx, int field, void *dev_out);
 
 /* Autotuner (no counterpart in the paper; the paper tunes its cell split
  * threshold by hand, Section 3.1). On the loaded state, times one
- * sph_density + sph_force for every combination of tile (0, 1; batched form
+ * sph_density + sph_force for every combination of tile (0, 1, 2; batched form
  * only), n_split (16, 32, 64, 128) and cell_factor (1.5, 2, 2.5, 3), each on its own
  * grid, best of 2, and keeps the fastest in the context's parameters; then
  * rebuilds the grid and leaves density and force computed on the current
