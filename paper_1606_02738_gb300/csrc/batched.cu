@@ -677,23 +677,31 @@ struct GroupCursor {
   }
 };
 
-// The stage is laid out in kNW segments of cap / kNW entries, warp w's staged
-// particles in segment w in the order that warp found them (deterministic).
-// A flat index t in [0, total) maps to segment entries through the prefix
-// counts pre[].
+// The stage is laid out in two halves of cap / 2 entries, one per pair of
+// warps: warp 0 fills the first half from its start upward and warp 1 from its
+// end downward, warps 2 and 3 the second half the same way, each in the order
+// it found its particles (deterministic). A pair overflows only when its two
+// shares together exceed the half, so a group fits when the larger pair sum
+// does (with a quarter of the stage per warp, the largest single share had
+// to). A flat index t in [0, total) (warp 0's entries, then warp 1's, 2's,
+// 3's) maps to its slot through the prefix counts pre[].
 struct StageRange {
   int total;      // staged entries, all warps
-  int over;       // some warp's share outgrew its segment (the stage is incomplete)
+  int over;       // some pair's shares outgrew its half (the stage is incomplete)
   int unmapped;   // (stored stage) some batch of tasks had no task map: slots not stored
-  int maxw;       // largest warp share
-  int segcap;     // entries per segment
-  int pre1, pre2, pre3;  // prefix counts of segments 0, 0..1, 0..2
+  int need;       // stage slots this group needs: 2 x the larger pair sum
+  int segcap;     // a quarter of the stage (a half holds 2 x segcap)
+  int pre1, pre2, pre3;  // prefix counts of warps 0, 0..1, 0..2
   __device__ __forceinline__ int index(int t) const {
-    const int off = t >= pre3 ? 3 * segcap - pre3
-                              : (t >= pre2 ? 2 * segcap - pre2 : (t >= pre1 ? segcap - pre1 : 0));
-    return t + off;
+    if (t < pre1) return t;                              // warp 0: upward from 0
+    if (t < pre2) return 2 * segcap - 1 + pre1 - t;      // warp 1: downward from the half
+    if (t < pre3) return 2 * segcap + t - pre2;          // warp 2: upward from the half
+    return 4 * segcap - 1 + pre3 - t;                    // warp 3: downward from the end
   }
 };
+__device__ __forceinline__ int stage_need(int c0, int c1, int c2, int c3) {
+  return 2 * max(c0 + c1, c2 + c3);
+}
 
 constexpr int kMap = 1024;  // per-warp particle -> task map (bytes, aliases the warp's cand)
 constexpr int kMapD = 2048; // the density's (its cand is larger)
@@ -710,8 +718,8 @@ static_assert(kStageD % kNW == 0 && kStageF % kNW == 0 && kBigStageD % kNW == 0 
 // marks its leaf's stretch in a shared-memory map, and the lanes then walk
 // the concatenated particles 32 at a time (kU loads in flight), reading each
 // particle's task from the map and the task's base and shift by shuffles.
-// Passing particles are appended to the warp's segment by ballot. Called by
-// every thread of the block.
+// Passing particles are appended by ballot at the warp's end of its pair's
+// half of the stage. Called by every thread of the block.
 // st_j / st_slot (density, first tier, neighbour cache): each staged
 // particle's index and task slot are also written there, at its stage slot.
 template <bool FORCE>
@@ -726,7 +734,10 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   const float4 *pm = FORCE ? fa->pm : da->pm;
   const int ntask = e1 - e0;
   const int segcap = cap / kNW;
-  const int base = warp * segcap;
+  const int half = 2 * segcap;
+  // this warp's k-th entry goes to slot sbase + sdir * k (k < half)
+  const int sdir = (warp & 1) ? -1 : 1;
+  const int sbase = (warp >> 1) * half + ((warp & 1) ? half - 1 : 0);
   constexpr int map_cap = FORCE ? kMap : kMapD;
   __syncthreads();  // every warp is done with the previous group's stage
   int nst = 0;
@@ -813,16 +824,17 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
         const int pos = nst + __popc(m & ltmask);
-        if (in && pos < segcap) {
-          sq[base + pos] = q[u];
+        if (in && pos < half) {  // within this pair's half (a pair that overflows is discarded)
+          const int slot = sbase + sdir * pos;
+          sq[slot] = q[u];
           if (FORCE) {
-            sf[base + pos] = make_float2(fj[u].z, fj[u].w);
-            sj[base + pos] = jj[u];
+            sf[slot] = make_float2(fj[u].z, fj[u].w);
+            sj[slot] = jj[u];
           }
           if (st_j) {  // the task of flat index f: from the map (else not stored)
-            st_j[base + pos] = jj[u];
+            st_j[slot] = jj[u];
             const int tl = mapped ? (int)tmap[f0 + 32 * u + lane] : 0;
-            st_slot[base + pos] = (unsigned short)(tb + tl * kNW);
+            st_slot[slot] = (unsigned short)(tb + tl * kNW);
           }
         }
         nst += __popc(m);
@@ -839,8 +851,8 @@ __device__ StageRange stage_group(const BatchDensArgs *da, const BatchForceArgs 
   r.pre2 = c0 + c1;
   r.pre3 = c0 + c1 + c2;
   r.total = r.pre3 + c3;
-  r.maxw = max(max(c0, c1), max(c2, c3));
-  r.over = r.maxw > segcap;
+  r.need = stage_need(c0, c1, c2, c3);
+  r.over = r.need > cap;
   r.unmapped = __syncthreads_or(unmapped);
   return r;
 }
@@ -967,7 +979,8 @@ struct DensAcc {
 };
 
 // Reload a group's stored stage (neighbour cache) into shared memory at the
-// current positions: entry k of segment w (k < wc[w]) is particle sj[k],
+// current positions: the stage slot k of warp w's entries (wc[w] of them, at
+// the slots of the staging layout) holds particle sj[k],
 // moved into the group frame by its task's shift (the same sum as the
 // staging, so the same FP32 values). The group's task shifts are first
 // copied to `shift` (shared memory free at this point, >= 3 ntask floats),
@@ -989,7 +1002,7 @@ __device__ StageRange load_stage_cached(const CacheArgs &C, int g, const int wc[
   r.pre2 = wc[0] + wc[1];
   r.pre3 = r.pre2 + wc[2];
   r.total = r.pre3 + wc[3];
-  r.maxw = max(max(wc[0], wc[1]), max(wc[2], wc[3]));
+  r.need = stage_need(wc[0], wc[1], wc[2], wc[3]);
   r.over = 0;
   r.unmapped = 0;
   for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
@@ -1146,7 +1159,7 @@ __global__ void __launch_bounds__(kNW * 32, dens_min_blocks(NS))
                               use_cache ? a.cache.sj + (size_t)g * a.cache.ns : nullptr,
                               use_cache ? a.cache.slot + (size_t)g * a.cache.ns : nullptr);
       if (use_cache && threadIdx.x == 0) {
-        for (int w = 0; w < 4; ++w) M->wc[w] = min(S.wcount[w], sr.segcap);
+        for (int w = 0; w < 4; ++w) M->wc[w] = min(S.wcount[w], 2 * sr.segcap);
         M->Rg = Rg;
         M->stage_ok = !sr.over && nt <= a.tcap && !sr.unmapped && !tightw;
         ++n_built;
@@ -2026,9 +2039,8 @@ __global__ void __launch_bounds__(kNW * 32, force_min_blocks(NS))
         stage_group<true>(nullptr, &a, G, e0, e0 + min(nt, a.tcap), warp, lane, G.hmax, S.sq,
                           S.sf, S.sj, S.wcount, (unsigned char *)cand, NS,
                           TIGHT ? S.tgt : nullptr);
-    // for tile 2: the stage this group needs (its warps' segments are equal, so
-    // the largest share decides whether it fits)
-    if (tier == 0 && a.gstage && threadIdx.x == 0) a.gstage[g] = sr.maxw * kNW;
+    // for tile 2: the stage this group needs (2 x the larger pair of warp shares)
+    if (tier == 0 && a.gstage && threadIdx.x == 0) a.gstage[g] = sr.need;
     stage_max = max(stage_max, sr.total);
     if (sr.over || nt > a.tcap) {  // block-uniform
       if (MID && nt <= a.tcap) {  // the tight stage outgrew this size: the large one

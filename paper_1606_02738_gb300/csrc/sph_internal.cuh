@@ -614,7 +614,7 @@ void launch_group_hmax(const GroupBuildArgs &a, cudaStream_t s);
 // rl - dpath_i - D: the kernel checks h_i against both and rebuilds the lists
 // (or sends the warp to the third tier) when h_i outgrows them.
 struct GroupCache {
-  int wc[4];       // staged entries per segment
+  int wc[4];       // staged entries per warp
   int tpad[4];     // stored list rows per warp (-1: none stored)
   int wok[4];      // the warp finished in the first tier on per-lane lists (last call)
   float Rg;        // stage radius at the build (distance from the group box)
