@@ -30,8 +30,8 @@
  *   - Particle arrays are in "caller order": particle k of box b is entry
  *     box_offsets[b] + k. Vectors are row-major [N][3].
  */
-#ifndef SPH_H
-#define SPH_H
+#ifndef SPH_ABI_H_INCLUDED
+#define SPH_ABI_H_INCLUDED
 
 #include <stddef.h>
 #include <stdint.h>
@@ -371,4 +371,4 @@ int sph_density_noalloc(int n, const double *box_len, const double *x, const flo
 }
 #endif
 
-#endif /* SPH_H */
+#endif /* SPH_ABI_H_INCLUDED */
